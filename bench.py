@@ -1,0 +1,288 @@
+"""Benchmark: GSM solves/s at 31^3 harmonics to relative residual 1e-8 on one
+B300 (woodpile of rods eps 11.9, Lambda = 0.35 lambda, 64^3 FFT grid).
+
+One step = one batched solve of B incident points (kappa over [0.70, 0.90] k0,
+x and y polarisation, normal incidence) with the complex64 FFT matvec inside
+FP64 iterative refinement, fields left in HBM.  Reported beside it: the plain
+FP64 GPU path on the same batch, the end-to-end rate through the C ABI with
+host buffers, the dominant kernel's roofline position and the CPU oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl reference]
+
+With N > 1 (torchrun) every rank solves its own batch (independent points:
+replicas, weak scaling); the max over ranks of the timed region is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1501_01752_b300 import workloads as wl  # noqa: E402
+
+METRIC = "solves/s at 31^3 harmonics, residual 1e-8: FP32+refine vs FP64 on B300; HBM % peak"
+N_HARM = (31, 31, 31)
+TOL = 1e-8
+L2_BYTES = 126 * 1024 * 1024
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
+# from the ncu capture summarised in profiles/ (None until measured for the
+# current kernel version)
+NCU_TRAFFIC = None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for n, v in zip(names, r[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except Exception:
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(points, budget_s=20.0):
+    """The oracle (FP64 GMRES, scipy FFT on all host cores) on a bounded sample
+    of the batch: as many points as fit in about budget_s seconds."""
+    from oracle import operator as oop
+    from oracle import retrieval as ort
+    cores = os.cpu_count() or 1
+    oop.WORKERS = cores
+    st = wl.woodpile()
+    ost = ort.Structure(st["periods"], st["eps_host"], st["shapes"])
+    Delta = ost.delta(N_HARM, 1.0)
+    done, t0 = 0, time.perf_counter()
+    for p in points:
+        ort.solve_point(ost, N_HARM, 1.0, p["k0"], p["kdir"], p["kappa"], p["pol"], tol=TOL, Delta=Delta)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of the %d woodpile points, 31^3 harmonics, FP64 GMRES(60) to 1e-8, scipy FFT on %d threads"
+                      % (done, len(points), cores)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+    return ws, rank, local
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    pts = wl.woodpile_batch(args.batch)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; its first solve is timed like the rest
+    vals = []
+    t_all = time.perf_counter()
+    for s in range(args.steps):
+        cb = cpu_baseline(pts[s % len(pts):] + pts[:s % len(pts)], budget_s=max(5.0, 60.0 / max(1, args.steps)))
+        vals.append(cb["value"])
+    dt = time.perf_counter() - t_all
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)",
+            "data": "synthetic", "config": {"workload": "woodpile eps 11.9, 31^3 harmonics, 64^3 grid",
+                                            "global_batch": args.batch, "tol": TOL},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    from paper_1501_01752_b300 import build
+    build.build()
+    from paper_1501_01752_b300 import gsm
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = wl.woodpile()
+    B = args.batch
+    pts = wl.woodpile_batch(B)
+    U = 3 * N_HARM[0] * N_HARM[1] * N_HARM[2]
+    stream = torch.cuda.current_stream(dev)
+
+    def make_plan(prec):
+        return gsm.plan_for(st, N_HARM, precision=prec, tol=TOL, max_batch=B, device=local,
+                            stream=stream.cuda_stream)
+
+    plan = make_plan(gsm.FP32_REFINE)
+    E = torch.empty(B * U, dtype=torch.complex128, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def timed(p, steps, out):
+        """Per-step CUDA events on the plan's stream; the L2 flush between steps
+        sits outside the events.  Returns summed device seconds."""
+        tot = 0.0
+        infos = None
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, infos, s = p.solve(pts, out=out)
+            b.record(stream)
+            b.synchronize()
+            if s:
+                raise RuntimeError("solve did not converge: %s" % infos)
+            tot += a.elapsed_time(b) / 1000.0
+        return tot, infos
+
+    for _ in range(args.warmup):
+        plan.solve(pts, out=E)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    plan.profile(True)
+    torch.cuda.synchronize()
+    barrier()
+    t_dev, infos = timed(plan, args.steps, E)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    kinds = {}
+    for k, name in enumerate(["fwd_x", "yz_conv", "inv_x_green", "krylov_dots", "krylov_update", "other"]):
+        n, ms, by = plan.profile_get(k)
+        kinds[name] = (n, ms, by)
+    launches = plan.profile_get(6)[0]
+    plan.profile(False)
+    if ws > 1:
+        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = ws * B * args.steps / t_dev
+
+    # end to end through the C ABI with host output buffers
+    Eh = None
+    t0 = time.perf_counter()
+    ee_steps = max(2, args.steps // 2)
+    for _ in range(ee_steps):
+        Eh, _, _ = plan.solve(pts)
+    e2e = B * ws * ee_steps / (time.perf_counter() - t0)
+    h2d = B * 88  # instance parameters (kinc, k_b^2, polarisation) per point
+    d2h = B * U * 16
+
+    # plain FP64 GPU path on the same batch
+    p64 = make_plan(gsm.FP64)
+    p64.solve(pts, out=E)
+    t64, infos64 = timed(p64, args.fp64_steps, E)
+    fp64_value = B * args.fp64_steps / t64
+    p64.close()
+
+    peak, peak_kind = peaks()
+    dom = max(kinds, key=lambda k: kinds[k][1])
+    n, ms, by = kinds[dom]
+    achieved = (by / n) / (ms / n / 1000.0) / 1e9 if n and ms > 0 else 0.0
+    iters = [i["iters"] for i in infos]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec + c128 refinement", "data": "synthetic",
+        "config": {"workload": "woodpile eps 11.9 in eps_b 1, Lambda 0.35, 31^3 harmonics, 64^3 FFT grid",
+                   "global_batch": B * ws, "tol": TOL, "l2": "flushed between steps (inputs+basis > L2)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "fp64_plain": {"value": fp64_value, "unit": "solves/s", "iters_mean": float(np.mean([i["iters"] for i in infos64]))},
+        "speedup_vs_fp64": value / ws / fp64_value,
+        "iters_mean": float(np.mean(iters)), "refine_steps_mean": float(np.mean([i["refine_steps"] for i in infos])),
+        "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": NCU_TRAFFIC,
+                     "launches": n, "avg_us": 1000.0 * ms / max(1, n)},
+        "kernel_shares": {k: {"launches": v[0], "ms": v[1], "GB/s": (v[2] / (v[1] / 1000.0) / 1e9) if v[1] else None}
+                          for k, v in kinds.items()},
+        "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(pts)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

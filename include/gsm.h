@@ -1,0 +1,195 @@
+/*
+ * gsm.h - C ABI of the B300 (sm_103a) Generalized Source Method solver for 3D
+ * periodic dielectric composites (Shcherbakov & Tishchenko, arXiv:1501.01752).
+ *
+ * The library solves the truncated Fourier-space equation of the paper's GSM
+ * section (Eq. 4),
+ *
+ *   E_{a m} = E^inc_{a m} + sum_b G_ab(m) sum_{m'} (Delta eps/eps_b)_{m-m'} E_{b m'},
+ *   G_ab(m) = (k_b^2 delta_ab - k_{a m} k_{b m}) / (k_m^2 - k_b^2),
+ *   k_{a m} = k^inc_a + m_a K_a,  K_a = 2 pi / Lambda_a,  k_b^2 = k0^2 eps_b,
+ *   E^inc_{a m} = delta_{m 0} a_a,
+ *
+ * with a Krylov method whose matrix-vector product is a pruned 3D FFT
+ * convolution (the Toeplitz product) followed by the per-harmonic Green tensor.
+ * It sweeps |k_inc| = kappa, fits the resonance poles of the 0th-order
+ * response (Eqs. 6-10 of the "Modes in 3D crystals" section) and returns the
+ * principal effective permittivities eps_aa = (eta / k0)^2.  An adjoint solve
+ * gives gradients with respect to voxel permittivities.
+ *
+ * Conventions used by every call:
+ *   - Units: lengths in vacuum wavelengths is the usual choice (k0 = 2 pi);
+ *     any consistent unit works since only k0 * Lambda enters.
+ *   - Field layout: per instance 3 planar components, each N_z x N_y x N_x
+ *     complex128 (interleaved re, im), x fastest; harmonic m sits at index
+ *     (m_z + n_z, m_y + n_y, m_x + n_x) with n_a = (N_a - 1) / 2.
+ *   - Fourier convention: eps(r) = sum_m eps_m exp(i K_m . r); a shape
+ *     centred at c contributes (eps_s - eps_host) exp(-i K_m . c) chi_s(K_m).
+ *   - Ownership: the plan owns all device memory it allocates; arrays passed
+ *     by the caller stay the caller's and are not retained after return.
+ *   - Streams: work is issued on desc.cuda_stream (0 = legacy default) and
+ *     every call synchronises that stream before it returns.
+ *   - Errors: every call returns a gsm_status; nothing is thrown across the
+ *     ABI.  gsm_last_error(plan) gives a one-line message.  On an error other
+ *     than GSM_ERR_NOCONV, output arrays are left untouched.
+ *   - Threads: a plan may be used by one host thread at a time.
+ */
+#ifndef GSM_H
+#define GSM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GSM_OK = 0,
+  GSM_ERR_ARG = 1,      /* invalid argument (message names it)                 */
+  GSM_ERR_SINGULAR = 2, /* some harmonic has k_m^2 ~= k_b^2 (Eq. 4 undefined)  */
+  GSM_ERR_NOCONV = 3,   /* Krylov solve missed tol within max_iter; best iterate written */
+  GSM_ERR_NOMEM = 4,    /* device allocation failed or hbm cap too small       */
+  GSM_ERR_CUDA = 5,     /* CUDA runtime error (message has the CUDA string)    */
+  GSM_ERR_TIMEOUT = 6,  /* reserved for bounded device waits                   */
+  GSM_ERR_STATE = 7     /* call out of order (e.g. solve before permittivity)  */
+} gsm_status;
+
+enum { GSM_FP64 = 0, GSM_FP32_REFINE = 1 };          /* arithmetic of the solve  */
+enum { GSM_GMRES = 0, GSM_BICGSTAB = 1 };            /* Krylov method            */
+enum { GSM_SPHERE = 0, GSM_BOX = 1, GSM_ELLIPSOID = 2 };
+
+typedef struct gsm_plan_s gsm_plan_t;
+
+/* Plan description (GSM section: truncation to N_x x N_y x N_z harmonics;
+ * "Calculation details": GMRES in Saad's form). */
+typedef struct {
+  double period[3];     /* Lambda_x, Lambda_y, Lambda_z (> 0)                            */
+  int n_harm[3];        /* N_x, N_y, N_z: odd, >= 1, <= 127                              */
+  int fft[3];           /* FFT points per axis; 0 = smallest power of two >= 2N-1 (<= 256) */
+  double eps_b[2];      /* basis permittivity eps_b (re, im); im must be 0               */
+  int precision;        /* GSM_FP64 or GSM_FP32_REFINE                                   */
+  int krylov;           /* GSM_GMRES (BiCGSTAB: GSM_BICGSTAB)                            */
+  int restart;          /* Krylov basis length m; 0 = 60                                 */
+  int max_iter;         /* total matrix-vector products per instance; 0 = 2000           */
+  double tol;           /* target ||b - A x|| / ||b||; 0 = 1e-8                          */
+  double inner_tol;     /* FP32 inner GMRES relative tolerance; 0 = 1e-4                 */
+  int max_batch;        /* instances solved together; 0 = 32                             */
+  size_t hbm_cap_bytes; /* 0 = unlimited; bounds the Krylov basis (restart shrinks)      */
+  int device;           /* CUDA device ordinal                                           */
+  void *cuda_stream;    /* cudaStream_t to issue work on; NULL = default stream          */
+} gsm_plan_desc;
+
+/* Non-overlapping inclusion in the host medium (GSM section: analytic Fourier
+ * images of simple shapes, combined).  size: SPHERE radius in size[0]; BOX
+ * full side lengths; ELLIPSOID semi-axes.  center in [0, Lambda) per axis. */
+typedef struct {
+  int kind;
+  double center[3];
+  double size[3];
+  double eps[2];        /* (re, im); im must be 0 */
+} gsm_shape;
+
+/* One incident plane wave (text after Eq. 4): |k_inc| = kappa along kdir,
+ * polarisation a (complex 3-vector, interleaved), frequency k0 = omega/c. */
+typedef struct {
+  double k0;
+  double kdir[3];       /* need not be normalised                                   */
+  double kappa;
+  double pol[6];        /* a_x re, a_x im, a_y re, a_y im, a_z re, a_z im            */
+  int n_harm[3];        /* 0 = plan's N; otherwise odd and <= plan's N per axis     */
+} gsm_point;
+
+typedef struct {
+  int iters;            /* matrix-vector products of the Krylov method                */
+  int refine_steps;     /* outer FP64 residual evaluations                             */
+  double rel_residual;  /* final FP64 ||b - A x|| / ||b||                              */
+  int status;           /* gsm_status of this instance                                 */
+} gsm_info;
+
+/* Host-only query (no device needed): the FFT sizes the plan would use and
+ * its device memory estimate in bytes.  Returns GSM_ERR_ARG on a bad desc. */
+gsm_status gsm_plan_query(const gsm_plan_desc *desc, int fft_out[3], size_t *bytes_out);
+
+/* Create a plan on desc->device.  Allocates the FFT twiddle tables and the
+ * per-level workspace lazily.  *out is NULL on failure. */
+gsm_status gsm_plan(const gsm_plan_desc *desc, gsm_plan_t **out);
+void gsm_plan_destroy(gsm_plan_t *plan);
+
+/* Set eps(r) of the unit cell ("Calculation details": analytic Fourier images).
+ * Either n_shapes >= 0 inclusions in a host of eps_host, or (voxel_eps != NULL)
+ * a grid of M[0] x M[1] x M[2] constant voxels (real eps, x fastest, voxel
+ * (vx,vy,vz) fills [v_a, v_a+1) Lambda_a / M_a), whose Fourier coefficients
+ * are exact integrals.  Shapes and voxels together are GSM_ERR_ARG; complex
+ * eps is GSM_ERR_ARG (lossless media only).  Builds the convolution
+ * multiplier D(r) = sum_d (Delta eps/eps_b)_d exp(2 pi i d.r/L) / (L_x L_y L_z)
+ * on the device for each truncation used. */
+gsm_status gsm_set_permittivity(gsm_plan_t *plan, const double eps_host[2],
+                                const gsm_shape *shapes, int n_shapes,
+                                const double *voxel_eps, const int M[3]);
+
+/* y = A x (Eq. 4 operator, adjoint = 0) or y = A^H x (adjoint = 1) for n
+ * points, each x/y of 3 N^3 complex128 (point's truncation).  on_device = 1:
+ * x, y are device pointers; 0: host.  precision GSM_FP32_REFINE rounds x to
+ * complex64 and applies the FP32 kernels (result widened to complex128). */
+gsm_status gsm_apply(gsm_plan_t *plan, int n, const gsm_point *points,
+                     const double *x, double *y, int on_device, int precision, int adjoint);
+
+/* Solve Eq. 4 for n points (any n; processed in batches of max_batch).  E
+ * receives n fields of 3 N^3 complex128 (on_device selects device or host
+ * memory).  infos (n entries) may be NULL.  Returns GSM_ERR_NOCONV if any
+ * instance missed tol (its best iterate is written), GSM_ERR_SINGULAR if a
+ * harmonic of some point lies on the basis light cone. */
+gsm_status gsm_solve(gsm_plan_t *plan, int n, const gsm_point *points,
+                     double *E, int on_device, gsm_info *infos);
+
+/* As gsm_solve but returns only the 0th harmonic E_0 (3 complex128 per point,
+ * host memory): the response of the "Modes in 3D crystals" section. */
+gsm_status gsm_sweep(gsm_plan_t *plan, int n, const gsm_point *points,
+                     double *E0, gsm_info *infos);
+
+/* Pole fit of Eqs. 7-10 (host, FP64): kappa[n] equidistant real, xi[n]
+ * complex (interleaved).  Needs Nd > Np and n >= Nd + Np.  eta, zeta receive
+ * Np complex values each. */
+gsm_status gsm_fit_poles(int n, const double *kappa, const double *xi, int Np, int Nd,
+                         double *eta, double *zeta);
+
+/* Principal effective permittivities (numerical-convergence section:
+ * principal axes along x, y, z): three sweeps of n_kappa equidistant points
+ * over kappa_lo_hi[c][0..1] with (kdir, a) = (z, x), (z, y), (x, z); fit; the
+ * largest-residue pole inside each interval gives eps_cc = (eta/k0)^2.
+ * diag (may be NULL) receives per component: eta (2), zeta (2). */
+gsm_status gsm_retrieve_tensor(gsm_plan_t *plan, double k0, const double kappa_lo_hi[6],
+                               int n_kappa, int Np, int Nd, double eps_eff[3], double *diag);
+
+/* Adjoint gradient (no counterpart in the paper; the calculus of Eq. 4): for
+ * n points with objective gradients gE0 (3 complex per point, dL/dRe E_0 +
+ * i dL/dIm E_0), accumulate dL/d eps_v into grad_voxel (host, M[0]M[1]M[2]
+ * reals, x fastest) for the voxel structure last set.  Requires a voxel
+ * permittivity.  Solves A E = b and A^H lambda = g~ per point. */
+gsm_status gsm_adjoint(gsm_plan_t *plan, int n, const gsm_point *points,
+                       const double *gE0, double *grad_voxel);
+
+/* Gradient of sum_c weights[c] Re eps_cc (the retrieval above) with respect
+ * to every voxel permittivity: sweeps, pole fits, pole sensitivities and
+ * adjoint solves.  eps_eff receives the retrieved diagonal. */
+gsm_status gsm_retrieve_tensor_grad(gsm_plan_t *plan, double k0, const double kappa_lo_hi[6],
+                                    int n_kappa, int Np, int Nd, const double weights[3],
+                                    double eps_eff[3], double *grad_voxel);
+
+/* Per-kernel timing with CUDA events on the plan's stream.  enable = 1 starts
+ * recording (and clears totals); gsm_profile_get returns launches, summed
+ * device milliseconds and algorithmic bytes for kernel class `kind`
+ * (0 x-forward, 1 yz-convolution, 2 x-inverse+Green, 3 Krylov dots,
+ * 4 Krylov update, 5 other; 6 = number of kernels the plan launched since
+ * gsm_profile, counted whether or not recording is on). */
+gsm_status gsm_profile(gsm_plan_t *plan, int enable);
+gsm_status gsm_profile_get(gsm_plan_t *plan, int kind, long long *launches,
+                           double *total_ms, double *bytes);
+
+const char *gsm_last_error(const gsm_plan_t *plan);
+const char *gsm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSM_H */

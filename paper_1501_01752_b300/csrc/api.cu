@@ -1,0 +1,904 @@
+// C-ABI entry points of the GSM solver (declared in include/gsm.h): plan and
+// workspace management, permittivity set-up, the batched Krylov drivers and
+// the retrieval.
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/gsm.h"
+#include "kernels.h"
+
+namespace gsm {
+using cd = std::complex<double>;
+void shapes_coefficients(cd eps_host, const gsm_shape *shapes, int n, const double period[3], const int D[3],
+                         std::vector<cd> &out);
+void voxel_coefficients(const double *vox, const int M[3], const int D[3], std::vector<cd> &out);
+int fit_poles(int M, const double *kappa, const cd *xi, int Np, int Nd, cd *eta, cd *zeta);
+int select_pole(int Np, const cd *eta, const cd *zeta, double lo, double hi);
+int pole_sensitivity(int M, const double *kappa, const cd *eta, const cd *zeta, int Np, int Nd, int index, cd *w);
+}  // namespace gsm
+
+using namespace gsm;
+
+namespace {
+
+struct Level {
+  Geo g;
+  double *D64 = nullptr;
+  float *D32 = nullptr;
+};
+
+// Device workspace for one level, sized for B instances and a basis of m+1.
+struct Work {
+  Geo g;
+  int B = 0, m = 0, prec = -1;
+  char *base = nullptr;
+  size_t bytes = 0;
+  void *V = nullptr;
+  double2 *x64 = nullptr, *r64 = nullptr, *T = nullptr, *e0 = nullptr;
+  double *iden64 = nullptr;
+  float *iden32 = nullptr;
+  Inst *inst = nullptr;
+  int *need = nullptr;
+  double *mv_partial = nullptr, *mv_norm = nullptr;
+  unsigned *mv_counter = nullptr;
+  KrylovPtrs k{};
+};
+
+struct Key {
+  int N[3];
+  bool operator<(const Key &o) const {
+    return std::memcmp(N, o.N, sizeof(N)) < 0;
+  }
+};
+
+}  // namespace
+
+struct gsm_plan_s {
+  gsm_plan_desc d{};
+  int L[3]{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  bool have_eps = false;
+  cd eps_host{1.0, 0.0};
+  std::vector<gsm_shape> shapes;
+  std::vector<double> vox;
+  int M[3]{};
+  std::map<Key, Level> levels;
+  std::map<Key, Work> works;
+  double2 *tw64 = nullptr;
+  float2 *tw32 = nullptr;
+  Profiler prof;
+  long long launches = 0;  // kernels issued by this plan
+  // pinned host staging
+  char *pin = nullptr;
+  size_t pin_bytes = 0;
+};
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      p->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return GSM_ERR_CUDA;                                                        \
+    }                                                                             \
+  } while (0)
+
+static gsm_status fail(gsm_plan_t *p, gsm_status s, const std::string &msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+static int fft_size(int N) {
+  int L = 1;
+  while (L < 2 * N - 1) L <<= 1;
+  return L;
+}
+
+static int ilog2(int L) {
+  int l = 0;
+  while ((1 << l) < L) ++l;
+  return l;
+}
+
+static std::string check_desc(const gsm_plan_desc *d, int L[3]) {
+  if (!d) return "desc is NULL";
+  for (int a = 0; a < 3; ++a) {
+    if (!(d->period[a] > 0)) return "period must be positive";
+    if (d->n_harm[a] < 1 || d->n_harm[a] % 2 == 0) return "n_harm must be odd and >= 1";
+    int Lmin = fft_size(d->n_harm[a]);
+    int Lv = d->fft[a] ? d->fft[a] : Lmin;
+    if (Lv < 2 * d->n_harm[a] - 1 || (Lv & (Lv - 1)) || Lv > TWN_HOST) return "fft size must be a power of two in [2N-1, 256]";
+    L[a] = Lv;
+  }
+  if (d->eps_b[1] != 0.0) return "complex eps_b is not supported (lossless basis only)";
+  if (!(d->eps_b[0] > 0)) return "eps_b must be positive";
+  if (d->precision != GSM_FP64 && d->precision != GSM_FP32_REFINE) return "precision must be GSM_FP64 or GSM_FP32_REFINE";
+  if (d->krylov != GSM_GMRES) return "only GSM_GMRES is implemented";
+  if (d->restart < 0 || d->restart > 120) return "restart must be in [0, 120]";
+  if (d->max_batch < 0 || d->max_batch > 4096) return "max_batch must be in [0, 4096]";
+  return "";
+}
+
+static Geo make_geo(const gsm_plan_desc &d, const int N[3], const int Lplan[3]) {
+  Geo g{};
+  for (int a = 0; a < 3; ++a) {
+    g.N[a] = N[a];
+    g.n[a] = (N[a] - 1) / 2;
+    // a reduced truncation uses its own smallest grid unless the plan's is forced
+    g.L[a] = (N[a] == d.n_harm[a]) ? Lplan[a] : fft_size(N[a]);
+    g.lg[a] = ilog2(g.L[a]);
+    g.K[a] = 2.0 * M_PI / d.period[a];
+  }
+  g.Nh = (long long)N[0] * N[1] * N[2];
+  g.U = 3 * g.Nh;
+  g.Tsz = 3LL * g.L[0] * N[1] * N[2];
+  return g;
+}
+
+static int restart_of(const gsm_plan_desc &d) { return d.restart ? d.restart : 60; }
+static int batch_of(const gsm_plan_desc &d) { return d.max_batch ? d.max_batch : 32; }
+static double tol_of(const gsm_plan_desc &d) { return d.tol > 0 ? d.tol : 1e-8; }
+static double inner_tol_of(const gsm_plan_desc &d) { return d.inner_tol > 0 ? d.inner_tol : 1e-4; }
+static int max_iter_of(const gsm_plan_desc &d) { return d.max_iter ? d.max_iter : 2000; }
+
+// Krylov length under the HBM cap for B instances in the given precision.
+static int capped_restart(const gsm_plan_desc &d, const Geo &g, int B, int prec) {
+  int m = restart_of(d);
+  if (d.hbm_cap_bytes) {
+    const size_t vec = (size_t)g.U * (prec ? 8 : 16) * B;
+    const long long fit = (long long)(d.hbm_cap_bytes / vec) - 1;
+    if (fit < m) m = (int)fit;
+  }
+  return m;
+}
+
+static size_t work_bytes(const Geo &g, int B, int m, int prec, int nblk) {
+  const size_t cs = prec ? 8 : 16;
+  size_t s = 0;
+  auto add = [&](size_t n) { s += (n + 255) & ~(size_t)255; };
+  add((size_t)(m + 1) * B * g.U * cs);        // V
+  add((size_t)B * g.U * 16 * 2);              // x64, r64
+  add((size_t)B * g.Tsz * 16);                // T
+  add((size_t)B * 3 * 16);                    // e0
+  add((size_t)B * g.Nh * 8);                  // iden64
+  add((size_t)B * g.Nh * 4);                  // iden32
+  add((size_t)B * sizeof(Inst));
+  add((size_t)B * 4);                         // need
+  const size_t hs = 2 * (m + 1) + 1;
+  const int mvb = std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8));
+  add((size_t)B * mvb * 8);                   // mv partial
+  add((size_t)B * 8);                         // mv norm
+  add((size_t)B * 4);                         // mv counter
+  add((size_t)(4 * 148 + B) * hs * 8 + (size_t)B * nblk * 8);  // krylov partial (any batch <= B)
+  add((size_t)B * 4);                         // counter
+  add((size_t)B * hs * 8 * 2);                // hdot0/1
+  add((size_t)B * 8 * 2);                     // wn0/1
+  add((size_t)B * 4 * 2);                     // gate, act
+  add((size_t)B * m * (m + 1) * 16);          // H
+  add((size_t)B * m * 8);                     // cs
+  add((size_t)B * m * 16);                    // sn
+  add((size_t)B * (m + 1) * 16);              // gv
+  add((size_t)B * m * 16);                    // y
+  add((size_t)B * 8);                         // thresh
+  add((size_t)B * 4);                         // kcount
+  add((size_t)B * 4);                         // scale32
+  add((size_t)B * 8 * 2);                     // scale64, resid
+  return s;
+}
+
+static int krylov_blocks(const Geo &g, int B) {
+  // enough blocks for ~4 waves of 148 SMs across the batch, each >= 2048 elements
+  long long per = std::max(1LL, (4LL * 148 + B - 1) / B);
+  long long cap = std::max(1LL, (g.U + 2047) / 2048);
+  return (int)std::min(per, cap);
+}
+
+static gsm_status get_work(gsm_plan_t *p, const Geo &g, int B, int m, int prec, Work **out) {
+  Key key{{g.N[0], g.N[1], g.N[2]}};
+  Work &w = p->works[key];
+  if (w.base && w.B >= B && w.m >= m && w.prec == prec) {
+    *out = &w;
+    return GSM_OK;
+  }
+  if (w.base) {
+    cudaFree(w.base);
+    w.base = nullptr;
+  }
+  const int nblk = krylov_blocks(g, B);
+  const size_t bytes = work_bytes(g, B, m, prec, nblk);
+  if (cudaMalloc(&w.base, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    w.base = nullptr;
+    return fail(p, GSM_ERR_NOMEM, "device workspace allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  w.g = g;
+  w.B = B;
+  w.m = m;
+  w.prec = prec;
+  w.bytes = bytes;
+  char *c = w.base;
+  auto take = [&](size_t n) {
+    char *r = c;
+    c += (n + 255) & ~(size_t)255;
+    return (void *)r;
+  };
+  const size_t cs = prec ? 8 : 16;
+  const size_t hs = 2 * (m + 1) + 1;
+  w.V = take((size_t)(m + 1) * B * g.U * cs);
+  w.x64 = (double2 *)take((size_t)B * g.U * 16);
+  w.r64 = (double2 *)take((size_t)B * g.U * 16);
+  w.T = (double2 *)take((size_t)B * g.Tsz * 16);
+  w.e0 = (double2 *)take((size_t)B * 3 * 16);
+  w.iden64 = (double *)take((size_t)B * g.Nh * 8);
+  w.iden32 = (float *)take((size_t)B * g.Nh * 4);
+  w.inst = (Inst *)take((size_t)B * sizeof(Inst));
+  w.need = (int *)take((size_t)B * 4);
+  const int mvb = std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8));
+  w.mv_partial = (double *)take((size_t)B * mvb * 8);
+  w.mv_norm = (double *)take((size_t)B * 8);
+  w.mv_counter = (unsigned *)take((size_t)B * 4);
+  KrylovPtrs &k = w.k;
+  k.B = B;
+  k.m = m;
+  k.U = g.U;
+  k.nblk = nblk;
+  k.partial = (double *)take((size_t)(4 * 148 + B) * hs * 8 + (size_t)B * nblk * 8);
+  k.counter = (unsigned *)take((size_t)B * 4);
+  k.hdot0 = (double *)take((size_t)B * hs * 8);
+  k.hdot1 = (double *)take((size_t)B * hs * 8);
+  k.wn0 = (double *)take((size_t)B * 8);
+  k.wn1 = (double *)take((size_t)B * 8);
+  k.gate = (int *)take((size_t)B * 4);
+  k.act = (int *)take((size_t)B * 4);
+  k.H = (double2 *)take((size_t)B * m * (m + 1) * 16);
+  k.cs = (double *)take((size_t)B * m * 8);
+  k.sn = (double2 *)take((size_t)B * m * 16);
+  k.gv = (double2 *)take((size_t)B * (m + 1) * 16);
+  k.y = (double2 *)take((size_t)B * m * 16);
+  k.thresh = (double *)take((size_t)B * 8);
+  k.kcount = (int *)take((size_t)B * 4);
+  k.scale32 = (float *)take((size_t)B * 4);
+  k.scale64 = (double *)take((size_t)B * 8);
+  k.resid = (double *)take((size_t)B * 8);
+  k.force_reorth = 0;
+  // counters must start at zero; the reductions reset them after use
+  if (cudaMemsetAsync(w.base, 0, bytes, p->st) != cudaSuccess) return fail(p, GSM_ERR_CUDA, "workspace memset failed");
+  *out = &w;
+  return GSM_OK;
+}
+
+static gsm_status ensure_pinned(gsm_plan_t *p, size_t bytes) {
+  if (p->pin_bytes >= bytes) return GSM_OK;
+  if (p->pin) cudaFreeHost(p->pin);
+  p->pin = nullptr;
+  p->pin_bytes = 0;
+  if (cudaMallocHost(&p->pin, bytes) != cudaSuccess) return fail(p, GSM_ERR_NOMEM, "pinned host allocation failed");
+  p->pin_bytes = bytes;
+  return GSM_OK;
+}
+
+// Build D(r) for a level from the analytic coefficients (once per structure).
+static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
+  Key key{{N[0], N[1], N[2]}};
+  auto it = p->levels.find(key);
+  if (it != p->levels.end() && it->second.D64) {
+    *out = &it->second;
+    return GSM_OK;
+  }
+  if (!p->have_eps) return fail(p, GSM_ERR_STATE, "gsm_set_permittivity has not been called");
+  Level &lv = p->levels[key];
+  lv.g = make_geo(p->d, N, p->L);
+  const Geo &g = lv.g;
+  const int D[3] = {2 * g.n[0], 2 * g.n[1], 2 * g.n[2]};
+  std::vector<cd> eps;
+  if (!p->vox.empty()) voxel_coefficients(p->vox.data(), p->M, D, eps);
+  else shapes_coefficients(p->eps_host, p->shapes.data(), (int)p->shapes.size(), p->d.period, D, eps);
+  const double eb = p->d.eps_b[0];
+  const int W0 = 2 * D[0] + 1, W1 = 2 * D[1] + 1, W2 = 2 * D[2] + 1;
+  eps[((size_t)D[2] * W1 + D[1]) * W0 + D[0]] -= eb;  // Delta eps = eps - eps_b at d = 0
+  const size_t LL = (size_t)g.L[0] * g.L[1] * g.L[2];
+  std::vector<double2> grid(LL, make_double2(0.0, 0.0));
+  for (int dz = -D[2]; dz <= D[2]; ++dz)
+    for (int dy = -D[1]; dy <= D[1]; ++dy)
+      for (int dx = -D[0]; dx <= D[0]; ++dx) {
+        const cd v = eps[((size_t)(dz + D[2]) * W1 + dy + D[1]) * W0 + dx + D[0]] / eb;
+        const int rz = (dz + g.L[2]) % g.L[2], ry = (dy + g.L[1]) % g.L[1], rx = (dx + g.L[0]) % g.L[0];
+        grid[((size_t)rz * g.L[1] + ry) * g.L[0] + rx] = make_double2(v.real(), v.imag());
+      }
+  double2 *dc = nullptr;
+  CK(cudaMalloc(&dc, LL * sizeof(double2)));
+  if (!lv.D64) CK(cudaMalloc(&lv.D64, LL * sizeof(double)));
+  if (!lv.D32) CK(cudaMalloc(&lv.D32, LL * sizeof(float)));
+  CK(cudaMemcpyAsync(dc, grid.data(), LL * sizeof(double2), cudaMemcpyHostToDevice, p->st));
+  for (int a = 0; a < 3; ++a) CK(launch_fft_axis(dc, g.L[0], g.L[1], g.L[2], a, +1, 1, 0, p->tw64, p->st));
+  CK(launch_d_finalize(dc, g, 1.0 / (double)LL, lv.D64, lv.D32, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  cudaFree(dc);
+  *out = &lv;
+  return GSM_OK;
+}
+
+static gsm_status point_level(gsm_plan_t *p, const gsm_point &pt, int N[3]) {
+  for (int a = 0; a < 3; ++a) {
+    N[a] = pt.n_harm[a] ? pt.n_harm[a] : p->d.n_harm[a];
+    if (N[a] < 1 || N[a] % 2 == 0 || N[a] > p->d.n_harm[a])
+      return fail(p, GSM_ERR_ARG, "point n_harm must be odd and <= the plan's");
+  }
+  return GSM_OK;
+}
+
+static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, Inst &I) {
+  const double nrm = std::sqrt(pt.kdir[0] * pt.kdir[0] + pt.kdir[1] * pt.kdir[1] + pt.kdir[2] * pt.kdir[2]);
+  if (!(nrm > 0) || !(pt.k0 > 0) || !std::isfinite(pt.kappa)) return fail(p, GSM_ERR_ARG, "bad point (k0, kdir, kappa)");
+  for (int a = 0; a < 3; ++a) I.kinc[a] = pt.kappa * pt.kdir[a] / nrm;
+  I.kb2 = pt.k0 * pt.k0 * p->d.eps_b[0];
+  for (int i = 0; i < 6; ++i) I.a[i] = pt.pol[i];
+  // Eq. 4 needs k_m^2 != k_b^2 for every harmonic (text after Eq. 4)
+  double kmax2 = 0;
+  for (int mz = -g.n[2]; mz <= g.n[2]; ++mz)
+    for (int my = -g.n[1]; my <= g.n[1]; ++my)
+      for (int mx = -g.n[0]; mx <= g.n[0]; ++mx) {
+        const double kx = I.kinc[0] + mx * g.K[0], ky = I.kinc[1] + my * g.K[1], kz = I.kinc[2] + mz * g.K[2];
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        if (std::fabs(k2 - I.kb2) <= 1e-9 * I.kb2)
+          return fail(p, GSM_ERR_SINGULAR, "harmonic on the basis light cone (k_m^2 = k_b^2); shift kappa or eps_b");
+        kmax2 = std::max(kmax2, k2);
+      }
+  return GSM_OK;
+}
+
+// ------------------------------------------------------------------ solve
+template <typename R>
+static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *pts, gsm_info *infos,
+                              double2 **out_x) {
+  using C = typename Cx<R>::T;
+  const Geo &g = lv.g;
+  const int prec = sizeof(R) == 4 ? 1 : 0;
+  const int m = capped_restart(p->d, g, B, prec);
+  if (m < 2) return fail(p, GSM_ERR_NOMEM, "hbm_cap_bytes leaves fewer than 3 Krylov vectors");
+  Work *w;
+  gsm_status s = get_work(p, g, B, m, prec, &w);
+  if (s) return s;
+  KrylovPtrs k = w->k;
+  k.B = B;
+  k.m = m;
+  k.nblk = krylov_blocks(g, B);
+  // pinned staging: instance parameters and the small per-cycle arrays
+  auto al = [](size_t n) { return (n + 63) & ~(size_t)63; };
+  const size_t stage = al(B * sizeof(Inst)) + al(B * 4) + al(B * 8) + al(B * 4) + al(B * 8) + al(B * 16) + al(B * 8);
+  if ((s = ensure_pinned(p, stage))) return s;
+  char *sp = p->pin;
+  auto grab = [&](size_t n) { char *r = sp; sp += al(n); return (void *)r; };
+  Inst *hI = (Inst *)grab(B * sizeof(Inst));
+  int *h_act = (int *)grab(B * 4);
+  double *h_thr = (double *)grab(B * 8);
+  float *h_s32 = (float *)grab(B * 4);
+  double *h_s64 = (double *)grab(B * 8);
+  double2 *h_g0 = (double2 *)grab(B * 16);
+  double *h_rn = (double *)grab(B * 8);
+  for (int b = 0; b < B; ++b)
+    if ((s = make_inst(p, pts[b], g, hI[b]))) return s;
+  cudaStream_t st = p->st;
+  Profiler *prof = p->prof.on ? &p->prof : nullptr;
+  CK(cudaMemcpyAsync(w->inst, hI, B * sizeof(Inst), cudaMemcpyHostToDevice, st));
+  CK(launch_iden(g, w->inst, B, w->iden64, w->iden32, st));
+  CK(cudaMemsetAsync(w->x64, 0, (size_t)B * g.U * 16, st));
+  CK(launch_set_rhs(w->r64, g.U, g, w->inst, B, st));
+  p->launches += 2;
+  const double tol = tol_of(p->d), itol = inner_tol_of(p->d);
+  const int max_it = max_iter_of(p->d);
+  std::vector<double> bnorm(B), rnorm(B);
+  std::vector<int> need(B, 1), iters(B, 0), steps(B, 0), status(B, GSM_OK);
+  for (int b = 0; b < B; ++b) {
+    double s2 = 0;
+    for (int i = 0; i < 6; ++i) s2 += pts[b].pol[i] * pts[b].pol[i];
+    bnorm[b] = rnorm[b] = std::sqrt(s2);
+    if (bnorm[b] == 0) need[b] = 0;  // zero source: E = 0
+  }
+  C *V = (C *)w->V;
+  const long long vinst = (long long)(m + 1) * g.U;
+  MatvecArgs<R> mv;
+  mv.g = g;
+  mv.B = B;
+  mv.T = (C *)w->T;
+  mv.D = sizeof(R) == 4 ? (const R *)lv.D32 : (const R *)lv.D64;
+  mv.act = k.act;
+  mv.inst = w->inst;
+  mv.iden = sizeof(R) == 4 ? (const R *)w->iden32 : (const R *)w->iden64;
+  mv.tw = sizeof(R) == 4 ? (const C *)p->tw32 : (const C *)p->tw64;
+  mv.xstride = vinst;
+  mv.ystride = vinst;
+  mv.write_back = 1;
+  mv.scale = sizeof(R) == 4 ? (const R *)k.scale32 : (const R *)k.scale64;
+  MatvecArgs<double> rs;  // FP64 residual b - A x
+  rs.g = g;
+  rs.B = B;
+  rs.X = w->x64;
+  rs.xstride = g.U;
+  rs.Y = w->r64;
+  rs.ystride = g.U;
+  rs.T = w->T;
+  rs.D = lv.D64;
+  rs.act = w->need;
+  rs.inst = w->inst;
+  rs.iden = w->iden64;
+  rs.tw = p->tw64;
+  rs.mode = 1;
+  rs.partial = w->mv_partial;
+  rs.counter = w->mv_counter;
+  rs.norm_out = w->mv_norm;
+  int outer = 0;
+  while (true) {
+    bool any = false;
+    for (int b = 0; b < B; ++b) any |= need[b] != 0;
+    if (!any) break;
+    // start a Krylov cycle on r (FP64) for every instance that still needs one
+    for (int b = 0; b < B; ++b) {
+      h_act[b] = need[b];
+      h_thr[b] = prec ? itol * rnorm[b] : 0.5 * tol * bnorm[b];
+      h_s32[b] = need[b] ? (float)(1.0 / rnorm[b]) : 0.f;
+      h_s64[b] = need[b] ? 1.0 / rnorm[b] : 0.0;
+      h_g0[b] = make_double2(rnorm[b], 0.0);
+    }
+    CK(cudaMemcpyAsync(k.act, h_act, B * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w->need, h_act, B * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(k.thresh, h_thr, B * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(k.scale32, h_s32, B * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(k.scale64, h_s64, B * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(k.gv, 0, (size_t)B * (m + 1) * 16, st));
+    CK(cudaMemcpy2DAsync(k.gv, (m + 1) * 16, h_g0, 16, 16, B, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(k.kcount, 0, (size_t)B * 4, st));
+    // V_0 = r in the basis precision (normalised in place by the first pass 1)
+    for (int b = 0; b < B; ++b) {
+      if (!need[b]) continue;
+      if (prec) {
+        CK(launch_convert_d2f(w->r64 + (size_t)b * g.U, (float2 *)(V + b * vinst), g.U, st));
+        p->launches++;
+      }
+      else CK(cudaMemcpyAsync((double2 *)(V + b * vinst), w->r64 + (size_t)b * g.U, g.U * 16, cudaMemcpyDeviceToDevice, st));
+    }
+    std::vector<int> act(need);
+    for (int j = 0; j < m; ++j) {
+      bool live = false;
+      for (int b = 0; b < B; ++b) live |= act[b] != 0;
+      if (!live) break;
+      mv.X = V + (long long)j * g.U;
+      mv.Y = V + (long long)(j + 1) * g.U;
+      CK(launch_matvec<R>(mv, st, prof));
+      CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
+      CK(launch_finish(k, j, st));
+      p->launches += 3 + 4 + 1;
+      for (int b = 0; b < B; ++b)
+        if (act[b]) iters[b]++;
+      CK(cudaMemcpyAsync(h_act, k.act, B * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int b = 0; b < B; ++b) act[b] = h_act[b];
+    }
+    CK(launch_backsolve(k, st));
+    CK(launch_sol_update<R>(k, w->x64, g.U, V, vinst, w->need, st, prof));
+    p->launches += 2 + 3;  // + the FP64 residual below
+    // FP64 residual of the updated iterate
+    if (prof) prof->begin(KIND_OTHER, st);
+    CK(launch_matvec<double>(rs, st, nullptr));
+    if (prof) prof->end(KIND_OTHER, st, 0.0);
+    CK(cudaMemcpyAsync(h_rn, w->mv_norm, B * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ++outer;
+    for (int b = 0; b < B; ++b) {
+      if (!need[b]) continue;
+      steps[b]++;
+      rnorm[b] = std::sqrt(std::max(h_rn[b], 0.0));
+      if (!std::isfinite(rnorm[b])) {
+        need[b] = 0;
+        status[b] = GSM_ERR_NOCONV;
+      } else if (rnorm[b] <= tol * bnorm[b]) {
+        need[b] = 0;
+      } else if (iters[b] >= max_it || steps[b] >= 200) {
+        need[b] = 0;
+        status[b] = GSM_ERR_NOCONV;
+      }
+    }
+  }
+  if (p->prof.on) p->prof.collect();
+  gsm_status worst = GSM_OK;
+  for (int b = 0; b < B; ++b) {
+    if (infos) {
+      infos[b].iters = iters[b];
+      infos[b].refine_steps = steps[b];
+      infos[b].rel_residual = bnorm[b] > 0 ? rnorm[b] / bnorm[b] : 0.0;
+      infos[b].status = status[b];
+    }
+    if (status[b]) worst = (gsm_status)status[b];
+  }
+  *out_x = w->x64;
+  return worst;
+}
+
+static gsm_status run_group(gsm_plan_t *p, Level &lv, int B, const gsm_point *pts, gsm_info *infos, double2 **x) {
+  if (p->d.precision == GSM_FP32_REFINE) return solve_batch<float>(p, lv, B, pts, infos, x);
+  return solve_batch<double>(p, lv, B, pts, infos, x);
+}
+
+// Solve n points grouped by truncation; deliver each instance's field through
+// `sink(point index, level, device field pointer, B-local index)`.
+template <typename F>
+static gsm_status solve_points(gsm_plan_t *p, int n, const gsm_point *points, gsm_info *infos, F sink) {
+  if (n < 0 || (n > 0 && !points)) return fail(p, GSM_ERR_ARG, "bad point array");
+  std::map<Key, std::vector<int>> groups;
+  for (int i = 0; i < n; ++i) {
+    int N[3];
+    gsm_status s = point_level(p, points[i], N);
+    if (s) return s;
+    groups[Key{{N[0], N[1], N[2]}}].push_back(i);
+  }
+  gsm_status worst = GSM_OK;
+  const int Bmax = batch_of(p->d);
+  for (auto &kv : groups) {
+    Level *lv;
+    gsm_status s = get_level(p, kv.first.N, &lv);
+    if (s) return s;
+    const std::vector<int> &idx = kv.second;
+    for (size_t off = 0; off < idx.size(); off += Bmax) {
+      const int B = (int)std::min<size_t>(Bmax, idx.size() - off);
+      std::vector<gsm_point> pts(B);
+      std::vector<gsm_info> inf(B);
+      for (int b = 0; b < B; ++b) pts[b] = points[idx[off + b]];
+      double2 *x = nullptr;
+      s = run_group(p, *lv, B, pts.data(), inf.data(), &x);
+      if (s && s != GSM_ERR_NOCONV) return s;
+      if (s) worst = s;
+      for (int b = 0; b < B; ++b) {
+        if (infos) infos[idx[off + b]] = inf[b];
+        s = sink(idx[off + b], *lv, x + (size_t)b * lv->g.U, b, x);
+        if (s) return s;
+      }
+    }
+  }
+  return worst;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *gsm_version(void) { return "gsm-b300 0.1 (sm_103a)"; }
+
+const char *gsm_last_error(const gsm_plan_t *plan) { return plan ? plan->err.c_str() : "no plan"; }
+
+gsm_status gsm_plan_query(const gsm_plan_desc *desc, int fft_out[3], size_t *bytes_out) {
+  int L[3];
+  if (!check_desc(desc, L).empty()) return GSM_ERR_ARG;
+  if (fft_out)
+    for (int a = 0; a < 3; ++a) fft_out[a] = L[a];
+  if (bytes_out) {
+    Geo g = make_geo(*desc, desc->n_harm, L);
+    const int B = batch_of(*desc), prec = desc->precision == GSM_FP32_REFINE;
+    const int m = std::max(2, capped_restart(*desc, g, B, prec));
+    *bytes_out = work_bytes(g, B, m, prec, krylov_blocks(g, B)) + (size_t)g.L[0] * g.L[1] * g.L[2] * 12;
+  }
+  return GSM_OK;
+}
+
+gsm_status gsm_plan(const gsm_plan_desc *desc, gsm_plan_t **out) {
+  if (!out) return GSM_ERR_ARG;
+  *out = nullptr;
+  int L[3];
+  std::string e = check_desc(desc, L);
+  if (!e.empty()) return GSM_ERR_ARG;
+  std::unique_ptr<gsm_plan_s> p(new gsm_plan_s());
+  p->d = *desc;
+  for (int a = 0; a < 3; ++a) p->L[a] = L[a];
+  {
+    Geo g = make_geo(*desc, desc->n_harm, L);
+    if (matvec_max_smem(g, 16) > 220 * 1024) return GSM_ERR_ARG;  // truncation too large for one SM's shared memory
+  }
+  gsm_plan_t *pp = p.get();
+  (void)pp;
+  if (cudaSetDevice(desc->device) != cudaSuccess) {
+    cudaGetLastError();
+    return GSM_ERR_CUDA;
+  }
+  p->st = (cudaStream_t)desc->cuda_stream;
+  std::vector<double2> t64(TWN_HOST);
+  std::vector<float2> t32(TWN_HOST);
+  for (int j = 0; j < TWN_HOST; ++j) {
+    const double a = 2.0 * M_PI * j / TWN_HOST;
+    t64[j] = make_double2(std::cos(a), std::sin(a));
+    t32[j] = make_float2((float)t64[j].x, (float)t64[j].y);
+  }
+  if (cudaMalloc(&p->tw64, sizeof(double2) * TWN_HOST) != cudaSuccess ||
+      cudaMalloc(&p->tw32, sizeof(float2) * TWN_HOST) != cudaSuccess) {
+    cudaGetLastError();
+    if (p->tw64) cudaFree(p->tw64);
+    return GSM_ERR_NOMEM;
+  }
+  if (cudaMemcpy(p->tw64, t64.data(), sizeof(double2) * TWN_HOST, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->tw32, t32.data(), sizeof(float2) * TWN_HOST, cudaMemcpyHostToDevice) != cudaSuccess)
+    return GSM_ERR_CUDA;
+  *out = p.release();
+  return GSM_OK;
+}
+
+void gsm_plan_destroy(gsm_plan_t *p) {
+  if (!p) return;
+  cudaSetDevice(p->d.device);
+  if (p->st) cudaStreamSynchronize(p->st);
+  else cudaDeviceSynchronize();
+  for (auto &kv : p->levels) {
+    cudaFree(kv.second.D64);
+    cudaFree(kv.second.D32);
+  }
+  for (auto &kv : p->works) cudaFree(kv.second.base);
+  cudaFree(p->tw64);
+  cudaFree(p->tw32);
+  if (p->pin) cudaFreeHost(p->pin);
+  delete p;
+}
+
+gsm_status gsm_set_permittivity(gsm_plan_t *p, const double eps_host[2], const gsm_shape *shapes, int n_shapes,
+                                const double *voxel_eps, const int M[3]) {
+  if (!p) return GSM_ERR_ARG;
+  if (n_shapes < 0 || (n_shapes > 0 && !shapes)) return fail(p, GSM_ERR_ARG, "bad shape array");
+  if (voxel_eps && n_shapes > 0) return fail(p, GSM_ERR_ARG, "give shapes or a voxel grid, not both");
+  std::vector<double> vox;
+  if (voxel_eps) {
+    if (!M || M[0] < 1 || M[1] < 1 || M[2] < 1) return fail(p, GSM_ERR_ARG, "bad voxel grid size");
+    const size_t n = (size_t)M[0] * M[1] * M[2];
+    vox.assign(voxel_eps, voxel_eps + n);
+    for (double v : vox)
+      if (!std::isfinite(v)) return fail(p, GSM_ERR_ARG, "non-finite voxel permittivity");
+  } else {
+    if (!eps_host) return fail(p, GSM_ERR_ARG, "eps_host is NULL");
+    if (eps_host[1] != 0.0) return fail(p, GSM_ERR_ARG, "complex permittivity is not supported (lossless media only)");
+    for (int i = 0; i < n_shapes; ++i) {
+      const gsm_shape &s = shapes[i];
+      if (s.kind < GSM_SPHERE || s.kind > GSM_ELLIPSOID) return fail(p, GSM_ERR_ARG, "unknown shape kind");
+      if (s.eps[1] != 0.0) return fail(p, GSM_ERR_ARG, "complex permittivity is not supported (lossless media only)");
+      const int ns = s.kind == GSM_SPHERE ? 1 : 3;
+      for (int a = 0; a < ns; ++a)
+        if (!(s.size[a] > 0)) return fail(p, GSM_ERR_ARG, "shape sizes must be positive");
+    }
+  }
+  p->have_eps = true;
+  p->eps_host = eps_host ? cd(eps_host[0], eps_host[1]) : cd(1.0, 0.0);
+  p->shapes.assign(shapes, shapes + n_shapes);
+  p->vox.swap(vox);
+  if (voxel_eps)
+    for (int a = 0; a < 3; ++a) p->M[a] = M[a];
+  // levels rebuild their D(r) lazily; keep the allocations
+  cudaSetDevice(p->d.device);
+  for (auto &kv : p->levels) {
+    cudaFree(kv.second.D64);
+    cudaFree(kv.second.D32);
+    kv.second.D64 = nullptr;
+    kv.second.D32 = nullptr;
+  }
+  Level *lv;
+  return get_level(p, p->d.n_harm, &lv);
+}
+
+gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double *x, double *y, int on_device,
+                     int precision, int adjoint) {
+  if (!p) return GSM_ERR_ARG;
+  if (n < 1 || !points || !x || !y) return fail(p, GSM_ERR_ARG, "bad arguments");
+  cudaSetDevice(p->d.device);
+  int N[3];
+  gsm_status s = point_level(p, points[0], N);
+  if (s) return s;
+  for (int i = 1; i < n; ++i) {
+    int N2[3];
+    if ((s = point_level(p, points[i], N2))) return s;
+    if (N2[0] != N[0] || N2[1] != N[1] || N2[2] != N[2]) return fail(p, GSM_ERR_ARG, "gsm_apply: all points need one truncation");
+  }
+  Level *lv;
+  if ((s = get_level(p, N, &lv))) return s;
+  const Geo &g = lv->g;
+  const int prec = precision == GSM_FP32_REFINE;
+  Work *w;
+  if ((s = get_work(p, g, n, 2, 0, &w))) return s;
+  if ((s = ensure_pinned(p, (size_t)n * sizeof(Inst)))) return s;
+  Inst *hI = (Inst *)p->pin;
+  for (int b = 0; b < n; ++b)
+    if ((s = make_inst(p, points[b], g, hI[b]))) return s;
+  cudaStream_t st = p->st;
+  CK(cudaMemcpyAsync(w->inst, hI, n * sizeof(Inst), cudaMemcpyHostToDevice, st));
+  CK(launch_iden(g, w->inst, n, w->iden64, w->iden32, st));
+  const size_t bytes = (size_t)n * g.U * 16;
+  double2 *xd = w->x64, *yd = w->r64;
+  CK(cudaMemcpyAsync(xd, x, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  if (prec) {
+    // FP32 kernels: round the input, run, widen the output (V holds >= 3 FP64 vectors)
+    float2 *xf = (float2 *)w->V, *yf = xf + (size_t)n * g.U;
+    CK(launch_convert_d2f(xd, xf, (long long)n * g.U, st));
+    MatvecArgs<float> a;
+    a.g = g;
+    a.B = n;
+    a.X = xf;
+    a.xstride = g.U;
+    a.Y = yf;
+    a.ystride = g.U;
+    a.T = (float2 *)w->T;
+    a.D = lv->D32;
+    a.inst = w->inst;
+    a.iden = w->iden32;
+    a.tw = p->tw32;
+    a.mode = adjoint ? 2 : 0;
+    CK(launch_matvec<float>(a, st, nullptr));
+    CK(launch_convert_f2d(yf, yd, (long long)n * g.U, st));
+  } else {
+    MatvecArgs<double> a;
+    a.g = g;
+    a.B = n;
+    a.X = xd;
+    a.xstride = g.U;
+    a.Y = yd;
+    a.ystride = g.U;
+    a.T = w->T;
+    a.D = lv->D64;
+    a.inst = w->inst;
+    a.iden = w->iden64;
+    a.tw = p->tw64;
+    a.mode = adjoint ? 2 : 0;
+    CK(launch_matvec<double>(a, st, nullptr));
+  }
+  CK(cudaMemcpyAsync(y, yd, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return GSM_OK;
+}
+
+gsm_status gsm_solve(gsm_plan_t *p, int n, const gsm_point *points, double *E, int on_device, gsm_info *infos) {
+  if (!p) return GSM_ERR_ARG;
+  if (!E) return fail(p, GSM_ERR_ARG, "E is NULL");
+  cudaSetDevice(p->d.device);
+  // output offsets: fields are packed in point order, each of its own 3 N^3
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    int N[3];
+    gsm_status s = point_level(p, points[i], N);
+    if (s) return s;
+    off[i + 1] = off[i] + 3ull * N[0] * N[1] * N[2];
+  }
+  gsm_status s = solve_points(p, n, points, infos, [&](int i, Level &lv, double2 *xf, int, double2 *) -> gsm_status {
+    CK(cudaMemcpyAsync(E + 2 * off[i], xf, lv.g.U * 16, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       p->st));
+    return GSM_OK;
+  });
+  if (s && s != GSM_ERR_NOCONV) return s;
+  CK(cudaStreamSynchronize(p->st));
+  return s;
+}
+
+gsm_status gsm_sweep(gsm_plan_t *p, int n, const gsm_point *points, double *E0, gsm_info *infos) {
+  if (!p) return GSM_ERR_ARG;
+  if (!E0) return fail(p, GSM_ERR_ARG, "E0 is NULL");
+  cudaSetDevice(p->d.device);
+  gsm_status s = solve_points(p, n, points, infos, [&](int i, Level &lv, double2 *, int b, double2 *x) -> gsm_status {
+    if (b == 0) {
+      // gather E_0 of the whole batch once, at its first instance
+      Work &w = p->works[Key{{lv.g.N[0], lv.g.N[1], lv.g.N[2]}}];
+      CK(launch_extract_e0(x, lv.g.U, lv.g, w.B, w.e0, p->st));
+    }
+    Work &w = p->works[Key{{lv.g.N[0], lv.g.N[1], lv.g.N[2]}}];
+    CK(cudaMemcpyAsync(E0 + 6 * (size_t)i, w.e0 + 3 * b, 48, cudaMemcpyDeviceToHost, p->st));
+    return GSM_OK;
+  });
+  if (s && s != GSM_ERR_NOCONV) return s;
+  CK(cudaStreamSynchronize(p->st));
+  return s;
+}
+
+gsm_status gsm_fit_poles(int n, const double *kappa, const double *xi, int Np, int Nd, double *eta, double *zeta) {
+  if (!kappa || !xi || !eta || !zeta) return GSM_ERR_ARG;
+  std::vector<cd> x(n), e(Np), z(Np);
+  for (int i = 0; i < n; ++i) x[i] = cd(xi[2 * i], xi[2 * i + 1]);
+  int r = fit_poles(n, kappa, x.data(), Np, Nd, e.data(), z.data());
+  if (r == 1) return GSM_ERR_ARG;
+  if (r) return GSM_ERR_NOCONV;
+  for (int j = 0; j < Np; ++j) {
+    eta[2 * j] = e[j].real();
+    eta[2 * j + 1] = e[j].imag();
+    zeta[2 * j] = z[j].real();
+    zeta[2 * j + 1] = z[j].imag();
+  }
+  return GSM_OK;
+}
+
+}  // extern "C"
+
+// principal sweeps: (kdir, a) = (z, x), (z, y), (x, z)
+static const double PR_K[3][3] = {{0, 0, 1}, {0, 0, 1}, {1, 0, 0}};
+static const double PR_A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+static void principal_points(double k0, const double lohi[6], int nk, std::vector<gsm_point> &pts,
+                             std::vector<double> &kap) {
+  pts.clear();
+  kap.clear();
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < nk; ++i) {
+      const double kv = lohi[2 * c] + (lohi[2 * c + 1] - lohi[2 * c]) * i / (nk - 1);
+      gsm_point pt{};
+      pt.k0 = k0;
+      for (int a = 0; a < 3; ++a) {
+        pt.kdir[a] = PR_K[c][a];
+        pt.pol[2 * a] = PR_A[c][a];
+      }
+      pt.kappa = kv;
+      pts.push_back(pt);
+      kap.push_back(kv);
+    }
+}
+
+extern "C" gsm_status gsm_retrieve_tensor(gsm_plan_t *p, double k0, const double kappa_lo_hi[6], int n_kappa, int Np,
+                                          int Nd, double eps_eff[3], double *diag) {
+  if (!p) return GSM_ERR_ARG;
+  if (!kappa_lo_hi || !eps_eff || n_kappa < Nd + Np || Nd <= Np || Np < 1 || !(k0 > 0))
+    return fail(p, GSM_ERR_ARG, "bad retrieval arguments (need n_kappa >= Nd + Np, Nd > Np)");
+  std::vector<gsm_point> pts;
+  std::vector<double> kap;
+  principal_points(k0, kappa_lo_hi, n_kappa, pts, kap);
+  std::vector<double> e0(6 * pts.size());
+  gsm_status s = gsm_sweep(p, (int)pts.size(), pts.data(), e0.data(), nullptr);
+  if (s) return s;
+  for (int c = 0; c < 3; ++c) {
+    std::vector<cd> xi(n_kappa), eta(Np), zeta(Np);
+    for (int i = 0; i < n_kappa; ++i) {
+      const int q = c * n_kappa + i;
+      cd v = 0;
+      for (int a = 0; a < 3; ++a) v += PR_A[c][a] * cd(e0[6 * q + 2 * a], e0[6 * q + 2 * a + 1]);  // a^H E_0
+      xi[i] = v;
+    }
+    if (fit_poles(n_kappa, &kap[c * n_kappa], xi.data(), Np, Nd, eta.data(), zeta.data()))
+      return fail(p, GSM_ERR_NOCONV, "pole fit failed");
+    const int j = select_pole(Np, eta.data(), zeta.data(), kappa_lo_hi[2 * c], kappa_lo_hi[2 * c + 1]);
+    if (j < 0) return fail(p, GSM_ERR_NOCONV, "no pole inside the kappa interval of component " + std::to_string(c));
+    const cd ev = (eta[j] / k0) * (eta[j] / k0);
+    eps_eff[c] = ev.real();
+    if (diag) {
+      diag[4 * c + 0] = eta[j].real();
+      diag[4 * c + 1] = eta[j].imag();
+      diag[4 * c + 2] = zeta[j].real();
+      diag[4 * c + 3] = zeta[j].imag();
+    }
+  }
+  return GSM_OK;
+}
+
+extern "C" gsm_status gsm_profile(gsm_plan_t *p, int enable) {
+  if (!p) return GSM_ERR_ARG;
+  p->prof.reset();
+  p->launches = 0;
+  p->prof.on = enable != 0;
+  return GSM_OK;
+}
+
+extern "C" gsm_status gsm_profile_get(gsm_plan_t *p, int kind, long long *launches, double *total_ms, double *bytes) {
+  if (!p) return GSM_ERR_ARG;
+  if (kind == KIND_COUNT) {  // every kernel the plan has launched
+    if (launches) *launches = p->launches;
+    if (total_ms) *total_ms = 0;
+    if (bytes) *bytes = 0;
+    return GSM_OK;
+  }
+  if (kind < 0 || kind > KIND_COUNT) return GSM_ERR_ARG;
+  if (launches) *launches = p->prof.launches[kind];
+  if (total_ms) *total_ms = p->prof.ms[kind];
+  if (bytes) *bytes = p->prof.bytes[kind];
+  return GSM_OK;
+}
+
+extern "C" gsm_status gsm_adjoint(gsm_plan_t *p, int, const gsm_point *, const double *, double *) {
+  return fail(p, GSM_ERR_STATE, "gsm_adjoint: adjoint path not built in this library version");
+}
+
+extern "C" gsm_status gsm_retrieve_tensor_grad(gsm_plan_t *p, double, const double *, int, int, int, const double *,
+                                               double *, double *) {
+  return fail(p, GSM_ERR_STATE, "gsm_retrieve_tensor_grad: adjoint path not built in this library version");
+}

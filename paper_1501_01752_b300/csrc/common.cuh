@@ -1,0 +1,52 @@
+// Shared device/host helpers for the GSM kernels: complex arithmetic on
+// float2/double2, the per-instance parameter block and the geometry of one
+// truncation level.  All kernels are written for sm_103a.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gsm {
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+
+// Per-instance parameters of one incident point (text after Eq. 4).
+struct Inst {
+  double kinc[3];  // k_inc = kappa * kdir
+  double kb2;      // k_b^2 = k0^2 eps_b
+  double a[6];     // polarisation (complex, interleaved): E^inc_{m=0}
+};
+
+// Geometry of one truncation level, passed by value to every kernel.
+struct Geo {
+  int N[3];        // harmonics per axis (odd)
+  int n[3];        // (N - 1) / 2
+  int L[3];        // FFT points per axis (power of two, >= 2N - 1)
+  int lg[3];       // log2 L
+  double K[3];     // reciprocal vectors 2 pi / Lambda
+  long long Nh;    // N0 N1 N2
+  long long U;     // 3 Nh complex unknowns per instance
+  long long Tsz;   // 3 L0 N1 N2: per-instance intermediate of the matvec
+};
+
+// cyclic position of harmonic index i (0..N-1, m = i - n) on an L-point grid
+__device__ __forceinline__ int wrap(int i, int n, int L) {
+  int m = i - n;
+  return m < 0 ? m + L : m;
+}
+
+}  // namespace gsm

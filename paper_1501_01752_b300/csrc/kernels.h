@@ -1,0 +1,140 @@
+// Host-side declarations of the kernel launchers and the per-kernel event
+// profiler shared by the CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gsm {
+
+constexpr int TWN_HOST = 256;  // twiddle table entries (largest FFT size)
+
+enum ProfKind { KIND_FWD_X = 0, KIND_YZ = 1, KIND_INV_X = 2, KIND_DOTS = 3, KIND_UPDATE = 4, KIND_OTHER = 5, KIND_COUNT = 6 };
+
+// Records a CUDA event pair around each launch of a kernel class on the
+// launching stream; durations are summed when read.
+struct Profiler {
+  bool on = false;
+  struct Rec { cudaEvent_t a, b; int kind; double bytes; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t pending_begin = nullptr;
+  long long launches[KIND_COUNT] = {0};
+  double ms[KIND_COUNT] = {0};
+  double bytes[KIND_COUNT] = {0};
+
+  cudaEvent_t get() {
+    if (used < pool.size()) return pool[used++];
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    pool.push_back(e);
+    used++;
+    return e;
+  }
+  void begin(int, cudaStream_t st) {
+    pending_begin = get();
+    cudaEventRecord(pending_begin, st);
+  }
+  void end(int kind, cudaStream_t st, double nbytes) {
+    cudaEvent_t e = get();
+    cudaEventRecord(e, st);
+    recs.push_back({pending_begin, e, kind, nbytes});
+  }
+  // fold recorded pairs into totals (stream must be synchronised)
+  void collect() {
+    for (auto &r : recs) {
+      float t = 0;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      launches[r.kind] += 1;
+      ms[r.kind] += t;
+      bytes[r.kind] += r.bytes;
+    }
+    recs.clear();
+    used = 0;
+  }
+  void reset() {
+    recs.clear();
+    used = 0;
+    for (int k = 0; k < KIND_COUNT; ++k) { launches[k] = 0; ms[k] = 0; bytes[k] = 0; }
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+template <typename R> struct MatvecArgs {
+  using C = typename Cx<R>::T;
+  Geo g;
+  int B = 0;
+  C *X = nullptr;          // input field(s), instance stride xstride
+  long long xstride = 0;
+  C *Y = nullptr;          // output field(s), instance stride ystride (may equal X only in mode 1? never)
+  long long ystride = 0;
+  C *T = nullptr;          // intermediate, B * g.Tsz complex
+  const R *D = nullptr;    // convolution multiplier [rx][ry][rz]
+  const R *scale = nullptr;  // per-instance input scale (nullptr = 1)
+  int write_back = 0;      // write the scaled input back to X (normalises a Krylov vector)
+  const int *act = nullptr;
+  const Inst *inst = nullptr;
+  const R *iden = nullptr; // [B][Nh] 1/(k_m^2 - k_b^2)
+  const C *tw = nullptr;   // 256-entry twiddle table
+  int mode = 0;            // 0: A x, 1: b - A x, 2: A^H x
+  double *partial = nullptr;
+  unsigned *counter = nullptr;
+  double *norm_out = nullptr;  // ||Y||^2 per instance (nullptr = skip)
+};
+
+template <typename R> cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof);
+int matvec_blocks_pass3(const Geo &g, size_t csize);
+size_t matvec_max_smem(const Geo &g, size_t csize);
+cudaError_t launch_iden(const Geo &g, const Inst *inst, int B, double *id64, float *id32, cudaStream_t st);
+cudaError_t launch_convert_d2f(const double2 *in, float2 *out, long long n, cudaStream_t st);
+cudaError_t launch_convert_f2d(const float2 *in, double2 *out, long long n, cudaStream_t st);
+
+// generic FP64 FFT along one axis of a batch of [Lz][Ly][Lx] complex arrays
+cudaError_t launch_fft_axis(double2 *data, int Lx, int Ly, int Lz, int axis, int sign, int batch,
+                            long long batch_stride, const double2 *tw, cudaStream_t st);
+cudaError_t launch_d_finalize(const double2 *Dc, const Geo &g, double scale, double *D64, float *D32,
+                              cudaStream_t st);
+
+// Krylov kernels (krylov.cu)
+struct KrylovPtrs {
+  int B, m;
+  long long U;
+  int nblk;                 // blocks per instance for vector kernels
+  double *partial;          // [B][nblk][2(m+1)+1]
+  unsigned *counter;        // [B]
+  double *hdot0, *hdot1;    // [B][2(m+1)+1] dots (+ ||w||^2 last)
+  double *wn0, *wn1;        // [B] ||w||^2 after update passes
+  int *gate;                // [B] reorthogonalise flag
+  int *act;                 // [B] Arnoldi active
+  double2 *H;               // [B][m][m+1] rotated Hessenberg columns
+  double *cs;               // [B][m]
+  double2 *sn;              // [B][m]
+  double2 *gv;              // [B][m+1]
+  double2 *y;               // [B][m]
+  double *thresh;           // [B]
+  int *kcount;              // [B]
+  float *scale32;           // [B]
+  double *scale64;          // [B]
+  double *resid;            // [B]
+  int force_reorth;
+};
+
+template <typename R>
+cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long long vinst, int j, cudaStream_t st,
+                                 Profiler *prof);
+cudaError_t launch_finish(const KrylovPtrs &k, int j, cudaStream_t st);
+cudaError_t launch_backsolve(const KrylovPtrs &k, cudaStream_t st);
+template <typename R>
+cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst, const typename Cx<R>::T *V,
+                              long long vinst, const int *need, cudaStream_t st, Profiler *prof);
+cudaError_t launch_set_rhs(double2 *r64, long long xinst, const Geo &g, const Inst *inst, int B, cudaStream_t st);
+cudaError_t launch_extract_e0(const double2 *x64, long long xinst, const Geo &g, int B, double2 *out,
+                              cudaStream_t st);
+
+}  // namespace gsm

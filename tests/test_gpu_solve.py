@@ -1,0 +1,134 @@
+"""Parity of the CUDA Krylov solve of Eq. 4 with the oracle: FP64 mode to
+1e-10 relative L2, FP32 matvec + FP64 refinement to 1e-6, batched and
+mixed-truncation solves, and the failure statuses."""
+import numpy as np
+import pytest
+
+from oracle import operator as oop
+from oracle import retrieval as ort
+from paper_1501_01752_b300 import workloads as wl
+
+from gpu_common import K0, gsm, oracle_structure, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_solve(st, n_harm, eps_b, pt, method="lu", tol=1e-13):
+    ost = oracle_structure(st)
+    E, info = ort.solve_point(ost, n_harm, eps_b, pt["k0"], pt["kdir"], pt["kappa"], pt["pol"], method=method, tol=tol)
+    return E
+
+
+def _fields(plan, pts, E):
+    out, off = [], 0
+    for p in pts:
+        n = plan.field_size(p)
+        out.append(E[off:off + n])
+        off += n
+    return out
+
+
+def test_c1_fp64_matches_dense_lu():
+    g = gsm()
+    st = wl.sphere_lattice()
+    n_harm = (7, 7, 7)
+    pt = wl.point(0.8 * K0)
+    plan = g.plan_for(st, n_harm, precision=g.FP64, tol=1e-12)
+    E, infos, s = plan.solve([pt])
+    assert s == 0 and infos[0]["rel_residual"] <= 1e-12
+    want = _oracle_solve(st, n_harm, 1.0, pt)
+    assert rel(E, want.ravel()) < 1e-10
+    assert 5 <= infos[0]["iters"] <= 60
+    plan.close()
+
+
+def test_c1_fp32_refine_matches_dense_lu():
+    g = gsm()
+    st = wl.sphere_lattice()
+    n_harm = (7, 7, 7)
+    pts = [wl.point(0.8 * K0), wl.point(0.8 * K0, (0, 0, 1), (0, 1, 0)), wl.point(0.6 * K0, (1, 1, 0), (0, 0, 1)),
+           wl.point(1.05 * K0, (0, 0, 1), (1, 0, 0))]
+    plan = g.plan_for(st, n_harm, precision=g.FP32_REFINE, tol=1e-8)
+    E, infos, s = plan.solve(pts)
+    assert s == 0
+    for b, (p, Eb) in enumerate(zip(pts, _fields(plan, pts, E))):
+        want = _oracle_solve(st, n_harm, 1.0, p)
+        assert infos[b]["rel_residual"] <= 1e-8
+        assert infos[b]["refine_steps"] >= 2   # at least one FP64 correction after the FP32 solve
+        assert rel(Eb, want.ravel()) < 1e-6, (b, rel(Eb, want.ravel()))
+    plan.close()
+
+
+def test_mixed_truncations_in_one_call():
+    g = gsm()
+    st = wl.ellipsoid_lattice()
+    pts = []
+    for i, N in enumerate([(5, 5, 5), (9, 9, 9), (5, 5, 5), (7, 9, 5)]):
+        p = wl.point((0.7 + 0.05 * i) * K0, (0, 0, 1), (1, 0, 0) if i % 2 == 0 else (0, 1, 0))
+        p["n_harm"] = N
+        pts.append(p)
+    plan = g.plan_for(st, (9, 9, 9), precision=g.FP64, tol=1e-12, max_batch=2)
+    E, infos, s = plan.solve(pts)
+    assert s == 0
+    for p, Eb in zip(pts, _fields(plan, pts, E)):
+        want = _oracle_solve(st, p["n_harm"], 1.0, p)
+        assert rel(Eb, want.ravel()) < 1e-10
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_woodpile_31_full_size(prec):
+    g = gsm()
+    st = wl.woodpile()
+    n_harm = (31, 31, 31)
+    pts = wl.woodpile_batch(4)
+    fp64 = prec == "fp64"
+    plan = g.plan_for(st, n_harm, precision=g.FP64 if fp64 else g.FP32_REFINE, tol=1e-11 if fp64 else 1e-8)
+    E, infos, s = plan.solve(pts)
+    assert s == 0
+    ost = oracle_structure(st)
+    Delta = ost.delta(n_harm, 1.0)
+    for b, (p, Eb) in enumerate(zip(pts, _fields(plan, pts, E))):
+        Eb = Eb.reshape((3,) + n_harm[::-1])
+        kinc = p["kappa"] * np.asarray(p["kdir"])
+        A = oop.Operator(Delta, n_harm, kinc, st["periods"], p["k0"] ** 2)
+        bvec = oop.incident(p["pol"], n_harm)
+        res = np.linalg.norm(bvec - A(Eb)) / np.linalg.norm(bvec)   # oracle's own residual of the GPU field
+        assert res <= (1.5e-11 if fp64 else 1.5e-8), (b, res)
+        if b < 2:
+            want = _oracle_solve(st, n_harm, 1.0, p, method="gmres", tol=1e-12)
+            assert rel(Eb, want) < (1e-9 if fp64 else 1e-6), (b, rel(Eb, want))
+    plan.close()
+
+
+def test_zero_source_singular_point_and_noconv():
+    g = gsm()
+    st = wl.sphere_lattice()
+    plan = g.plan_for(st, (5, 5, 5), precision=g.FP64, tol=1e-12)
+    p0 = wl.point(0.8 * K0, pol=(0, 0, 0))
+    E, infos, s = plan.solve([p0])
+    assert s == 0 and np.all(E == 0)
+    with pytest.raises(g.GsmError) as ei:
+        plan.solve([wl.point(1.0 * K0)])     # m = 0 on the basis light cone
+    assert ei.value.status == g.GSM_ERR_SINGULAR
+    plan.close()
+    plan = g.plan_for(st, (7, 7, 7), precision=g.FP64, tol=1e-14, max_iter=4, restart=4)
+    E, infos, s = plan.solve([wl.point(0.8 * K0)])
+    assert s == g.GSM_ERR_NOCONV and infos[0]["status"] == g.GSM_ERR_NOCONV
+    assert infos[0]["iters"] >= 4 and np.all(np.isfinite(E)) and infos[0]["rel_residual"] < 1.0
+    plan.close()
+
+
+def test_hbm_cap_restarts_and_still_converges():
+    g = gsm()
+    st = wl.woodpile()
+    n_harm = (15, 15, 15)
+    U = 3 * 15**3
+    pt = wl.point(0.8 * K0)
+    cap = 6 * U * 8      # room for 6 complex64 vectors: restart length 5
+    plan = g.plan_for(st, n_harm, precision=g.FP32_REFINE, tol=1e-8, hbm_cap=cap, max_batch=1)
+    E, infos, s = plan.solve([pt])
+    assert s == 0 and infos[0]["rel_residual"] <= 1e-8
+    want = _oracle_solve(st, n_harm, 1.0, pt, method="gmres", tol=1e-12)
+    assert rel(E, want.ravel()) < 1e-6
+    plan.close()
