@@ -161,45 +161,71 @@ static int capped_restart(const gsm_plan_desc &d, const Geo &g, int B, int prec)
   return m;
 }
 
-static size_t work_bytes(const Geo &g, int B, int m, int prec, int nblk) {
-  const size_t cs = prec ? 8 : 16;
-  size_t s = 0;
-  auto add = [&](size_t n) { s += (n + 255) & ~(size_t)255; };
-  add((size_t)(m + 1) * B * g.U * cs);        // V
-  add((size_t)B * g.U * 16 * 2);              // x64, r64
-  add((size_t)B * g.Tsz * 16);                // T
-  add((size_t)B * 3 * 16);                    // e0
-  add((size_t)B * g.Nh * 8);                  // iden64
-  add((size_t)B * g.Nh * 4);                  // iden32
-  add((size_t)B * sizeof(Inst));
-  add((size_t)B * 4);                         // need
-  const size_t hs = 2 * (m + 1) + 1;
-  const int mvb = std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8));
-  add((size_t)B * mvb * 8);                   // mv partial
-  add((size_t)B * 8);                         // mv norm
-  add((size_t)B * 4);                         // mv counter
-  add((size_t)(4 * 148 + B) * hs * 8 + (size_t)B * nblk * 8);  // krylov partial (any batch <= B)
-  add((size_t)B * 4);                         // counter
-  add((size_t)B * hs * 8 * 2);                // hdot0/1
-  add((size_t)B * 8 * 2);                     // wn0/1
-  add((size_t)B * 4 * 2);                     // gate, act
-  add((size_t)B * m * (m + 1) * 16);          // H
-  add((size_t)B * m * 8);                     // cs
-  add((size_t)B * m * 16);                    // sn
-  add((size_t)B * (m + 1) * 16);              // gv
-  add((size_t)B * m * 16);                    // y
-  add((size_t)B * 8);                         // thresh
-  add((size_t)B * 4);                         // kcount
-  add((size_t)B * 4);                         // scale32
-  add((size_t)B * 8 * 2);                     // scale64, resid
-  return s;
-}
+static long long padded(long long U) { return ((U + 63) / 64) * 64; }
 
 static int krylov_blocks(const Geo &g, int B) {
   // enough blocks for ~4 waves of 148 SMs across the batch, each >= 2048 elements
   long long per = std::max(1LL, (4LL * 148 + B - 1) / B);
-  long long cap = std::max(1LL, (g.U + 2047) / 2048);
+  long long cap = std::max(1LL, (padded(g.U) + 2047) / 2048);
   return (int)std::min(per, cap);
+}
+
+// Carve the workspace of B instances out of `base` (nullptr: only measure).
+// The same routine sizes and assigns, so every array lies inside the block.
+static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nblk, char *base) {
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    void *r = base ? (void *)(base + off) : nullptr;
+    off += (n + 255) & ~(size_t)255;
+    return r;
+  };
+  const size_t cs = prec ? 8 : 16;
+  const size_t hs = 2 * (m + 1) + 1;
+  w.V = take((size_t)(m + 1) * B * padded(g.U) * cs);
+  w.x64 = (double2 *)take((size_t)B * g.U * 16);
+  w.r64 = (double2 *)take((size_t)B * g.U * 16);
+  w.T = (double2 *)take((size_t)B * g.Tsz * 16);
+  w.e0 = (double2 *)take((size_t)B * 3 * 16);
+  w.iden64 = (double *)take((size_t)B * g.Nh * 8);
+  w.iden32 = (float *)take((size_t)B * g.Nh * 4);
+  w.inst = (Inst *)take((size_t)B * sizeof(Inst));
+  w.need = (int *)take((size_t)B * 4);
+  const int mvb = std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8));
+  w.mv_partial = (double *)take((size_t)B * mvb * 8);
+  w.mv_norm = (double *)take((size_t)B * 8);
+  w.mv_counter = (unsigned *)take((size_t)B * 4);
+  KrylovPtrs &k = w.k;
+  k.B = B;
+  k.m = m;
+  k.U = g.U;
+  k.Us = padded(g.U);
+  k.nblk = nblk;
+  // partials for any batch <= B: B' * krylov_blocks(g, B') <= 4 * 148 + B'
+  k.partial = (double *)take((size_t)(4 * 148 + B) * hs * 8);
+  k.counter = (unsigned *)take((size_t)B * 4);
+  k.hdot0 = (double *)take((size_t)B * hs * 8);
+  k.hdot1 = (double *)take((size_t)B * hs * 8);
+  k.wn0 = (double *)take((size_t)B * 8);
+  k.wn1 = (double *)take((size_t)B * 8);
+  k.gate = (int *)take((size_t)B * 4);
+  k.act = (int *)take((size_t)B * 4);
+  k.H = (double2 *)take((size_t)B * m * (m + 1) * 16);
+  k.cs = (double *)take((size_t)B * m * 8);
+  k.sn = (double2 *)take((size_t)B * m * 16);
+  k.gv = (double2 *)take((size_t)B * (m + 1) * 16);
+  k.y = (double2 *)take((size_t)B * m * 16);
+  k.thresh = (double *)take((size_t)B * 8);
+  k.kcount = (int *)take((size_t)B * 4);
+  k.scale32 = (float *)take((size_t)B * 4);
+  k.scale64 = (double *)take((size_t)B * 8);
+  k.resid = (double *)take((size_t)B * 8);
+  k.force_reorth = 0;
+  return off;
+}
+
+static size_t work_bytes(const Geo &g, int B, int m, int prec, int nblk) {
+  Work tmp;
+  return work_layout(tmp, g, B, m, prec, nblk, nullptr);
 }
 
 static gsm_status get_work(gsm_plan_t *p, const Geo &g, int B, int m, int prec, Work **out) {
@@ -225,51 +251,7 @@ static gsm_status get_work(gsm_plan_t *p, const Geo &g, int B, int m, int prec, 
   w.m = m;
   w.prec = prec;
   w.bytes = bytes;
-  char *c = w.base;
-  auto take = [&](size_t n) {
-    char *r = c;
-    c += (n + 255) & ~(size_t)255;
-    return (void *)r;
-  };
-  const size_t cs = prec ? 8 : 16;
-  const size_t hs = 2 * (m + 1) + 1;
-  w.V = take((size_t)(m + 1) * B * g.U * cs);
-  w.x64 = (double2 *)take((size_t)B * g.U * 16);
-  w.r64 = (double2 *)take((size_t)B * g.U * 16);
-  w.T = (double2 *)take((size_t)B * g.Tsz * 16);
-  w.e0 = (double2 *)take((size_t)B * 3 * 16);
-  w.iden64 = (double *)take((size_t)B * g.Nh * 8);
-  w.iden32 = (float *)take((size_t)B * g.Nh * 4);
-  w.inst = (Inst *)take((size_t)B * sizeof(Inst));
-  w.need = (int *)take((size_t)B * 4);
-  const int mvb = std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8));
-  w.mv_partial = (double *)take((size_t)B * mvb * 8);
-  w.mv_norm = (double *)take((size_t)B * 8);
-  w.mv_counter = (unsigned *)take((size_t)B * 4);
-  KrylovPtrs &k = w.k;
-  k.B = B;
-  k.m = m;
-  k.U = g.U;
-  k.nblk = nblk;
-  k.partial = (double *)take((size_t)(4 * 148 + B) * hs * 8 + (size_t)B * nblk * 8);
-  k.counter = (unsigned *)take((size_t)B * 4);
-  k.hdot0 = (double *)take((size_t)B * hs * 8);
-  k.hdot1 = (double *)take((size_t)B * hs * 8);
-  k.wn0 = (double *)take((size_t)B * 8);
-  k.wn1 = (double *)take((size_t)B * 8);
-  k.gate = (int *)take((size_t)B * 4);
-  k.act = (int *)take((size_t)B * 4);
-  k.H = (double2 *)take((size_t)B * m * (m + 1) * 16);
-  k.cs = (double *)take((size_t)B * m * 8);
-  k.sn = (double2 *)take((size_t)B * m * 16);
-  k.gv = (double2 *)take((size_t)B * (m + 1) * 16);
-  k.y = (double2 *)take((size_t)B * m * 16);
-  k.thresh = (double *)take((size_t)B * 8);
-  k.kcount = (int *)take((size_t)B * 4);
-  k.scale32 = (float *)take((size_t)B * 4);
-  k.scale64 = (double *)take((size_t)B * 8);
-  k.resid = (double *)take((size_t)B * 8);
-  k.force_reorth = 0;
+  work_layout(w, g, B, m, prec, nblk, w.base);
   // counters must start at zero; the reductions reset them after use
   if (cudaMemsetAsync(w.base, 0, bytes, p->st) != cudaSuccess) return fail(p, GSM_ERR_CUDA, "workspace memset failed");
   *out = &w;
@@ -357,9 +339,12 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
 }
 
 // ------------------------------------------------------------------ solve
+// Solve A x = b (adj = false) or A^H x = b (adj = true) for B instances of
+// one level.  b = a at m = 0, with a the point's polarisation or, when rhs is
+// given, rhs[6 b .. 6 b + 5].
 template <typename R>
 static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *pts, gsm_info *infos,
-                              double2 **out_x) {
+                              double2 **out_x, bool adj, const double *rhs) {
   using C = typename Cx<R>::T;
   const Geo &g = lv.g;
   const int prec = sizeof(R) == 4 ? 1 : 0;
@@ -385,8 +370,11 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   double *h_s64 = (double *)grab(B * 8);
   double2 *h_g0 = (double2 *)grab(B * 16);
   double *h_rn = (double *)grab(B * 8);
-  for (int b = 0; b < B; ++b)
+  for (int b = 0; b < B; ++b) {
     if ((s = make_inst(p, pts[b], g, hI[b]))) return s;
+    if (rhs)
+      for (int i = 0; i < 6; ++i) hI[b].a[i] = rhs[6 * b + i];
+  }
   cudaStream_t st = p->st;
   Profiler *prof = p->prof.on ? &p->prof : nullptr;
   CK(cudaMemcpyAsync(w->inst, hI, B * sizeof(Inst), cudaMemcpyHostToDevice, st));
@@ -400,12 +388,15 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   std::vector<int> need(B, 1), iters(B, 0), steps(B, 0), status(B, GSM_OK);
   for (int b = 0; b < B; ++b) {
     double s2 = 0;
-    for (int i = 0; i < 6; ++i) s2 += pts[b].pol[i] * pts[b].pol[i];
+    for (int i = 0; i < 6; ++i) s2 += hI[b].a[i] * hI[b].a[i];
     bnorm[b] = rnorm[b] = std::sqrt(s2);
     if (bnorm[b] == 0) need[b] = 0;  // zero source: E = 0
   }
   C *V = (C *)w->V;
-  const long long vinst = (long long)(m + 1) * g.U;
+  const long long Us = padded(g.U);
+  const long long vinst = (long long)(m + 1) * Us;
+  CK(launch_zero_pads<C>(V, (long long)B * (m + 1), g.U, Us, st));
+  p->launches++;
   MatvecArgs<R> mv;
   mv.g = g;
   mv.B = B;
@@ -418,6 +409,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   mv.xstride = vinst;
   mv.ystride = vinst;
   mv.write_back = 1;
+  mv.mode = adj ? 2 : 0;
   mv.scale = sizeof(R) == 4 ? (const R *)k.scale32 : (const R *)k.scale64;
   MatvecArgs<double> rs;  // FP64 residual b - A x
   rs.g = g;
@@ -432,7 +424,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   rs.inst = w->inst;
   rs.iden = w->iden64;
   rs.tw = p->tw64;
-  rs.mode = 1;
+  rs.mode = adj ? 3 : 1;
   rs.partial = w->mv_partial;
   rs.counter = w->mv_counter;
   rs.norm_out = w->mv_norm;
@@ -471,8 +463,8 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       bool live = false;
       for (int b = 0; b < B; ++b) live |= act[b] != 0;
       if (!live) break;
-      mv.X = V + (long long)j * g.U;
-      mv.Y = V + (long long)(j + 1) * g.U;
+      mv.X = V + (long long)j * Us;
+      mv.Y = V + (long long)(j + 1) * Us;
       CK(launch_matvec<R>(mv, st, prof));
       CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
       CK(launch_finish(k, j, st));
@@ -523,15 +515,17 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   return worst;
 }
 
-static gsm_status run_group(gsm_plan_t *p, Level &lv, int B, const gsm_point *pts, gsm_info *infos, double2 **x) {
-  if (p->d.precision == GSM_FP32_REFINE) return solve_batch<float>(p, lv, B, pts, infos, x);
-  return solve_batch<double>(p, lv, B, pts, infos, x);
+static gsm_status run_group(gsm_plan_t *p, Level &lv, int B, const gsm_point *pts, gsm_info *infos, double2 **x,
+                            bool adj, const double *rhs) {
+  if (p->d.precision == GSM_FP32_REFINE) return solve_batch<float>(p, lv, B, pts, infos, x, adj, rhs);
+  return solve_batch<double>(p, lv, B, pts, infos, x, adj, rhs);
 }
 
 // Solve n points grouped by truncation; deliver each instance's field through
 // `sink(point index, level, device field pointer, B-local index)`.
 template <typename F>
-static gsm_status solve_points(gsm_plan_t *p, int n, const gsm_point *points, gsm_info *infos, F sink) {
+static gsm_status solve_points(gsm_plan_t *p, int n, const gsm_point *points, gsm_info *infos, F sink,
+                               bool adj = false, const double *rhs = nullptr) {
   if (n < 0 || (n > 0 && !points)) return fail(p, GSM_ERR_ARG, "bad point array");
   std::map<Key, std::vector<int>> groups;
   for (int i = 0; i < n; ++i) {
@@ -551,9 +545,14 @@ static gsm_status solve_points(gsm_plan_t *p, int n, const gsm_point *points, gs
       const int B = (int)std::min<size_t>(Bmax, idx.size() - off);
       std::vector<gsm_point> pts(B);
       std::vector<gsm_info> inf(B);
-      for (int b = 0; b < B; ++b) pts[b] = points[idx[off + b]];
+      std::vector<double> r6(rhs ? 6 * B : 0);
+      for (int b = 0; b < B; ++b) {
+        pts[b] = points[idx[off + b]];
+        if (rhs)
+          for (int i = 0; i < 6; ++i) r6[6 * b + i] = rhs[6 * (size_t)idx[off + b] + i];
+      }
       double2 *x = nullptr;
-      s = run_group(p, *lv, B, pts.data(), inf.data(), &x);
+      s = run_group(p, *lv, B, pts.data(), inf.data(), &x, adj, rhs ? r6.data() : nullptr);
       if (s && s != GSM_ERR_NOCONV) return s;
       if (s) worst = s;
       for (int b = 0; b < B; ++b) {
@@ -894,11 +893,136 @@ extern "C" gsm_status gsm_profile_get(gsm_plan_t *p, int kind, long long *launch
   return GSM_OK;
 }
 
-extern "C" gsm_status gsm_adjoint(gsm_plan_t *p, int, const gsm_point *, const double *, double *) {
-  return fail(p, GSM_ERR_STATE, "gsm_adjoint: adjoint path not built in this library version");
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0 && v <= TWN_HOST; }
+
+// Adjoint gradient for n points with objective gradients gE0 (6 doubles per
+// point): forward and adjoint solves per batch, correlation on the L grid,
+// fold onto the voxel grid, one voxel FFT.  grad (host) is accumulated.
+static gsm_status adjoint_impl(gsm_plan_t *p, int n, const gsm_point *points, const double *gE0, double *grad) {
+  if (p->vox.empty()) return fail(p, GSM_ERR_STATE, "gsm_adjoint needs a voxel permittivity");
+  if (!pow2(p->M[0]) || !pow2(p->M[1]) || !pow2(p->M[2]))
+    return fail(p, GSM_ERR_ARG, "gsm_adjoint needs power-of-two voxel grid sizes (<= 256)");
+  cudaStream_t st = p->st;
+  // every point at the plan's full truncation (one correlation grid)
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a)
+      if (points[i].n_harm[a] && points[i].n_harm[a] != p->d.n_harm[a])
+        return fail(p, GSM_ERR_ARG, "gsm_adjoint: points must use the plan's truncation");
+  Level *lv;
+  gsm_status s = get_level(p, p->d.n_harm, &lv);
+  if (s) return s;
+  const Geo g = lv->g;
+  const long long LL = (long long)g.L[0] * g.L[1] * g.L[2];
+  const long long MM = (long long)p->M[0] * p->M[1] * p->M[2];
+  double2 *Ef = nullptr, *grid = nullptr, *P = nullptr, *Q = nullptr;
+  double *outd = nullptr;
+  auto cleanup = [&]() { cudaFree(Ef); cudaFree(grid); cudaFree(P); cudaFree(Q); cudaFree(outd); };
+  if (cudaMalloc(&Ef, (size_t)n * g.U * 16) != cudaSuccess || cudaMalloc(&grid, (size_t)6 * LL * 16) != cudaSuccess ||
+      cudaMalloc(&P, (size_t)LL * 16) != cudaSuccess || cudaMalloc(&Q, (size_t)MM * 16) != cudaSuccess ||
+      cudaMalloc(&outd, (size_t)MM * 8) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(p, GSM_ERR_NOMEM, "gsm_adjoint: device allocation failed");
+  }
+  gsm_status worst = GSM_OK;
+  // forward fields
+  s = solve_points(p, n, points, nullptr, [&](int i, Level &, double2 *xf, int, double2 *) -> gsm_status {
+    CK(cudaMemcpyAsync(Ef + (size_t)i * g.U, xf, g.U * 16, cudaMemcpyDeviceToDevice, st));
+    return GSM_OK;
+  });
+  if (s && s != GSM_ERR_NOCONV) { cleanup(); return s; }
+  if (s) worst = s;
+  if (cudaMemsetAsync(P, 0, (size_t)LL * 16, st) != cudaSuccess) { cleanup(); return fail(p, GSM_ERR_CUDA, "memset"); }
+  // adjoint fields and their correlation with the forward ones
+  s = solve_points(
+      p, n, points, nullptr,
+      [&](int i, Level &lvl, double2 *lam, int b, double2 *) -> gsm_status {
+        Work &w = p->works[Key{{lvl.g.N[0], lvl.g.N[1], lvl.g.N[2]}}];
+        CK(cudaMemsetAsync(grid, 0, (size_t)6 * LL * 16, st));
+        CK(launch_adj_scatter(g, lam, Ef + (size_t)i * g.U, w.inst + b, w.iden64 + (size_t)b * g.Nh, grid, st));
+        CK(launch_fft_axis(grid, g.L[0], g.L[1], g.L[2], 0, +1, 6, LL, p->tw64, st));
+        CK(launch_fft_axis(grid, g.L[0], g.L[1], g.L[2], 1, +1, 6, LL, p->tw64, st));
+        CK(launch_fft_axis(grid, g.L[0], g.L[1], g.L[2], 2, +1, 6, LL, p->tw64, st));
+        CK(launch_adj_accum(grid, LL, P, st));
+        p->launches += 5;
+        return GSM_OK;
+      },
+      true, gE0);
+  if (s && s != GSM_ERR_NOCONV) { cleanup(); return s; }
+  if (s) worst = s;
+  for (int a = 0; a < 3; ++a)
+    if (cudaSuccess != launch_fft_axis(P, g.L[0], g.L[1], g.L[2], a, +1, 1, 0, p->tw64, st)) {
+      cleanup();
+      return fail(p, GSM_ERR_CUDA, "adjoint correlation FFT");
+    }
+  gsm_status rs = GSM_OK;
+  [&]() -> gsm_status {
+    CK(launch_adj_fold(P, g, p->M, Q, st));
+    for (int a = 0; a < 3; ++a) CK(launch_fft_axis(Q, p->M[0], p->M[1], p->M[2], a, -1, 1, 0, p->tw64, st));
+    CK(launch_adj_real(Q, MM, 1.0 / ((double)MM * p->d.eps_b[0]), outd, st));
+    std::vector<double> h(MM);
+    CK(cudaMemcpyAsync(h.data(), outd, MM * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (long long t = 0; t < MM; ++t) grad[t] += h[t];
+    return GSM_OK;
+  }() == GSM_OK ? (void)0 : (void)(rs = GSM_ERR_CUDA);
+  cleanup();
+  return rs ? rs : worst;
 }
 
-extern "C" gsm_status gsm_retrieve_tensor_grad(gsm_plan_t *p, double, const double *, int, int, int, const double *,
-                                               double *, double *) {
-  return fail(p, GSM_ERR_STATE, "gsm_retrieve_tensor_grad: adjoint path not built in this library version");
+extern "C" gsm_status gsm_adjoint(gsm_plan_t *p, int n, const gsm_point *points, const double *gE0,
+                                  double *grad_voxel) {
+  if (!p) return GSM_ERR_ARG;
+  if (n < 1 || !points || !gE0 || !grad_voxel) return fail(p, GSM_ERR_ARG, "bad adjoint arguments");
+  cudaSetDevice(p->d.device);
+  return adjoint_impl(p, n, points, gE0, grad_voxel);
+}
+
+extern "C" gsm_status gsm_retrieve_tensor_grad(gsm_plan_t *p, double k0, const double kappa_lo_hi[6], int n_kappa,
+                                               int Np, int Nd, const double weights[3], double eps_eff[3],
+                                               double *grad_voxel) {
+  if (!p) return GSM_ERR_ARG;
+  if (!kappa_lo_hi || !eps_eff || !weights || !grad_voxel || n_kappa < Nd + Np || Nd <= Np || Np < 1 || !(k0 > 0))
+    return fail(p, GSM_ERR_ARG, "bad retrieval arguments (need n_kappa >= Nd + Np, Nd > Np)");
+  cudaSetDevice(p->d.device);
+  std::vector<gsm_point> pts;
+  std::vector<double> kap;
+  principal_points(k0, kappa_lo_hi, n_kappa, pts, kap);
+  std::vector<double> e0(6 * pts.size());
+  gsm_status s = gsm_sweep(p, (int)pts.size(), pts.data(), e0.data(), nullptr);
+  if (s) return s;
+  std::vector<gsm_point> gp;
+  std::vector<double> g6;
+  for (int c = 0; c < 3; ++c) {
+    std::vector<cd> xi(n_kappa), eta(Np), zeta(Np), sens(n_kappa);
+    for (int i = 0; i < n_kappa; ++i) {
+      const int q = c * n_kappa + i;
+      cd v = 0;
+      for (int a = 0; a < 3; ++a) v += PR_A[c][a] * cd(e0[6 * q + 2 * a], e0[6 * q + 2 * a + 1]);
+      xi[i] = v;
+    }
+    if (fit_poles(n_kappa, &kap[c * n_kappa], xi.data(), Np, Nd, eta.data(), zeta.data()))
+      return fail(p, GSM_ERR_NOCONV, "pole fit failed");
+    const int j = select_pole(Np, eta.data(), zeta.data(), kappa_lo_hi[2 * c], kappa_lo_hi[2 * c + 1]);
+    if (j < 0) return fail(p, GSM_ERR_NOCONV, "no pole inside the kappa interval of component " + std::to_string(c));
+    eps_eff[c] = ((eta[j] / k0) * (eta[j] / k0)).real();
+    if (weights[c] == 0.0) continue;
+    if (pole_sensitivity(n_kappa, &kap[c * n_kappa], eta.data(), zeta.data(), Np, Nd, j, sens.data()))
+      return fail(p, GSM_ERR_NOCONV, "pole sensitivity failed");
+    // d Re eps / d xi_i = Re(q_i d xi_i), q_i = 2 eta s_i / k0^2; objective
+    // gradient with respect to E_0: conj(q_i) a
+    for (int i = 0; i < n_kappa; ++i) {
+      const cd q = weights[c] * 2.0 * eta[j] * sens[i] / (k0 * k0);
+      gp.push_back(pts[c * n_kappa + i]);
+      for (int a = 0; a < 3; ++a) {
+        const cd ga = std::conj(q) * PR_A[c][a];
+        g6.push_back(ga.real());
+        g6.push_back(ga.imag());
+      }
+    }
+  }
+  const long long MM = (long long)p->M[0] * p->M[1] * p->M[2];
+  for (long long t = 0; t < MM; ++t) grad_voxel[t] = 0.0;
+  if (gp.empty()) return GSM_OK;
+  return adjoint_impl(p, (int)gp.size(), gp.data(), g6.data(), grad_voxel);
 }

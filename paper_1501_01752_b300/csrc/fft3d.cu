@@ -8,7 +8,7 @@
 namespace gsm {
 
 template <int S>
-__global__ void k_fft_axis(double2 *data, int Lx, int Ly, int Lz, int axis, int lg, long long bstride, int nl,
+__global__ void __launch_bounds__(256) k_fft_axis(double2 *data, int Lx, int Ly, int Lz, int axis, int lg, long long bstride, int nl,
                            const double2 *__restrict__ twg) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   double2 *tw = reinterpret_cast<double2 *>(sm_raw);
@@ -53,7 +53,7 @@ cudaError_t launch_fft_axis(double2 *data, int Lx, int Ly, int Lz, int axis, int
   const long long nlines = axis == 0 ? (long long)Ly * Lz : (axis == 1 ? (long long)Lz * Lx : (long long)Ly * Lx);
   int nl = std::max(1, 4096 / L);
   const int ts = L >= 8 ? L / 8 : 1;
-  const int threads = std::min(1024, std::max(64, ((nl * ts + 31) / 32) * 32));
+  const int threads = std::min(256, std::max(64, ((nl * ts + 31) / 32) * 32));
   nl = std::min(nl, threads / ts);
   const size_t smem = sizeof(double2) * (TWN + (size_t)nl * (L + 1));
   dim3 grid((unsigned)((nlines + nl - 1) / nl), batch);

@@ -82,7 +82,7 @@ template <typename R> struct MatvecArgs {
   const Inst *inst = nullptr;
   const R *iden = nullptr; // [B][Nh] 1/(k_m^2 - k_b^2)
   const C *tw = nullptr;   // 256-entry twiddle table
-  int mode = 0;            // 0: A x, 1: b - A x, 2: A^H x
+  int mode = 0;            // 0: A x, 1: b - A x, 2: A^H x, 3: b - A^H x
   double *partial = nullptr;
   unsigned *counter = nullptr;
   double *norm_out = nullptr;  // ||Y||^2 per instance (nullptr = skip)
@@ -104,7 +104,8 @@ cudaError_t launch_d_finalize(const double2 *Dc, const Geo &g, double scale, dou
 // Krylov kernels (krylov.cu)
 struct KrylovPtrs {
   int B, m;
-  long long U;
+  long long U;              // logical vector length (3 N^3)
+  long long Us;             // stored stride: U rounded up to 64 (pads stay zero)
   int nblk;                 // blocks per instance for vector kernels
   double *partial;          // [B][nblk][2(m+1)+1]
   unsigned *counter;        // [B]
@@ -122,7 +123,7 @@ struct KrylovPtrs {
   float *scale32;           // [B]
   double *scale64;          // [B]
   double *resid;            // [B]
-  int force_reorth;
+  int force_reorth;         // 0: DGKS test, 1: always reorthogonalise, 2: never
 };
 
 template <typename R>
@@ -133,8 +134,17 @@ cudaError_t launch_backsolve(const KrylovPtrs &k, cudaStream_t st);
 template <typename R>
 cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst, const typename Cx<R>::T *V,
                               long long vinst, const int *need, cudaStream_t st, Profiler *prof);
+template <typename C>
+cudaError_t launch_zero_pads(C *V, long long nvec, long long U, long long Us, cudaStream_t st);
 cudaError_t launch_set_rhs(double2 *r64, long long xinst, const Geo &g, const Inst *inst, int B, cudaStream_t st);
 cudaError_t launch_extract_e0(const double2 *x64, long long xinst, const Geo &g, int B, double2 *out,
                               cudaStream_t st);
+
+// adjoint gradient (adjoint.cu)
+cudaError_t launch_adj_scatter(const Geo &g, const double2 *lam, const double2 *E, const Inst *inst, const double *iden,
+                               double2 *grid, cudaStream_t st);
+cudaError_t launch_adj_accum(const double2 *grid, long long LL, double2 *P, cudaStream_t st);
+cudaError_t launch_adj_fold(const double2 *P, const Geo &g, const int M[3], double2 *Q, cudaStream_t st);
+cudaError_t launch_adj_real(const double2 *Q, long long n, double scale, double *out, cudaStream_t st);
 
 }  // namespace gsm

@@ -14,8 +14,9 @@
 // reorthogonalisation test instead of the paper's modified Gram-Schmidt: the
 // j sequential dot/axpy pairs of MGS become two fused passes (four when the
 // test fires), with orthogonality at least as good as MGS.  Dots of FP32
-// vectors sum FP32 products in runs of 8 and accumulate the runs in FP64;
-// Hessenberg, rotations and residual estimates are FP64.  Reductions across
+// vectors sum FP32 products over one tile (2048 values: 8 per thread, then a
+// 32-lane tree) and accumulate the tile sums in FP64; Hessenberg, rotations
+// and residual estimates are FP64.  Reductions across
 // blocks use the last-block-done pattern (atomic counter, no waiting).
 #include "kernels.h"
 #include "reduce.cuh"
@@ -25,71 +26,104 @@ namespace gsm {
 constexpr int KT = 256;  // threads per block of the vector kernels
 constexpr int MAXM = 128;
 
-// Reduce K doubles per thread over the block; thread k < K gets total k in out[k].
-template <int K>
-__device__ __forceinline__ void block_reduce_k(double (&v)[K], double *red, double *out) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+// Vectors are stored with a stride Us (the length U rounded up to 64
+// complex values, pads held at zero), so each thread moves EPT consecutive
+// values with 16-byte loads: a tile is KT * EPT values.
+template <typename R> struct Ept { static constexpr int v = sizeof(R) == 4 ? 8 : 4; };
+
+template <typename C, int EPT> __device__ __forceinline__ void load_ept(C (&d)[EPT], const C *src) {
+  if constexpr (sizeof(C) == 8) {
+    const float4 *q = reinterpret_cast<const float4 *>(src);
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double t = v[k];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (l == 0) red[k * 32 + w] = t;
+    for (int k = 0; k < EPT / 2; ++k) {
+      const float4 t = q[k];
+      d[2 * k] = mk(t.x, t.y);
+      d[2 * k + 1] = mk(t.z, t.w);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) d[k] = src[k];
   }
-  __syncthreads();
-  if (threadIdx.x < K) {
-    double s = 0;
-    for (int i = 0; i < nw; ++i) s += red[threadIdx.x * 32 + i];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
 }
 
+template <typename C, int EPT> __device__ __forceinline__ void store_ept(C *dst, const C (&d)[EPT]) {
+  if constexpr (sizeof(C) == 8) {
+    float4 *q = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int k = 0; k < EPT / 2; ++k) q[k] = make_float4(d[2 * k].x, d[2 * k].y, d[2 * k + 1].x, d[2 * k + 1].y);
+  } else {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) dst[k] = d[k];
+  }
+}
+
+template <typename R> __device__ __forceinline__ R warp_sum(R v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// h_i = <v_i, w> for i < nv and ||w||^2: w is held in registers per tile,
+// every basis vector streamed once.  Products are summed in the basis
+// precision over one tile (EPT per thread, then a 32-lane tree) and the tile
+// sums are accumulated in FP64.
 template <typename R>
-__global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict__ V, long long vinst, long long U,
+__global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict__ V, long long vinst, long long Us,
                                              int nv, int wi, const int *__restrict__ act,
                                              const int *__restrict__ gate, double *partial, unsigned *counter,
                                              double *out, int ostride) {
   using C = typename Cx<R>::T;
-  __shared__ double red[9 * 32];
-  __shared__ double tot[9];
+  constexpr int EPT = Ept<R>::v, NW = KT / 32;
+  __shared__ double wsum[2 * MAXM + 3][NW];
   __shared__ int am_last;
   const int b = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
   if (!act[b]) return;
   if (gate && !gate[b]) return;
+  const int K = 2 * nv + 1, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < K * NW; k += blockDim.x) (&wsum[0][0])[k] = 0.0;
+  __syncthreads();
   const C *Vb = V + b * vinst;
-  const C *W = Vb + (long long)wi * U;
-  const long long chunk = (U + nblk - 1) / nblk;
-  const long long e0 = blk * chunk, e1 = min(U, e0 + chunk);
-  const int K = 2 * nv + 1;
-  double *pb = partial + ((long long)b * nblk + blk) * K;
-  for (int i0 = 0; i0 < nv; i0 += 4) {
-    double acc[9];
-    R run[9];
+  const C *W = Vb + (long long)wi * Us;
+  const long long ntiles = (Us + KT * EPT - 1) / (KT * EPT);
+  for (long long t = blk; t < ntiles; t += nblk) {
+    const long long e0 = t * (KT * EPT) + (long long)threadIdx.x * EPT;
+    const bool ok = e0 < Us;
+    C w[EPT];
+    if (ok) load_ept<C, EPT>(w, W + e0);
+    else
 #pragma unroll
-    for (int k = 0; k < 9; ++k) { acc[k] = 0; run[k] = 0; }
-    int cnt = 0;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const C w = W[e];
+      for (int k = 0; k < EPT; ++k) w[k] = mk((R)0, (R)0);
+    R n2 = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (i0 + k < nv) {
-          const C v = Vb[(long long)(i0 + k) * U + e];
-          run[2 * k] += v.x * w.x + v.y * w.y;      // conj(v) w
-          run[2 * k + 1] += v.x * w.y - v.y * w.x;
-        }
+    for (int k = 0; k < EPT; ++k) n2 += w[k].x * w[k].x + w[k].y * w[k].y;
+    n2 = warp_sum(n2);
+    if (lane == 0) wsum[2 * nv][warp] += (double)n2;
+    for (int i = 0; i < nv; ++i) {
+      C v[EPT];
+      if (ok) load_ept<C, EPT>(v, Vb + (long long)i * Us + e0);
+      else
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) v[k] = mk((R)0, (R)0);
+      R re = 0, im = 0;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        re += v[k].x * w[k].x + v[k].y * w[k].y;   // conj(v) w
+        im += v[k].x * w[k].y - v[k].y * w[k].x;
       }
-      if (i0 == 0) run[8] += w.x * w.x + w.y * w.y;
-      if (++cnt == 8) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) { acc[k] += (double)run[k]; run[k] = 0; }
-        cnt = 0;
+      re = warp_sum(re);
+      im = warp_sum(im);
+      if (lane == 0) {
+        wsum[2 * i][warp] += (double)re;
+        wsum[2 * i + 1][warp] += (double)im;
       }
     }
+  }
+  __syncthreads();
+  double *pb = partial + ((long long)b * nblk + blk) * K;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double s = 0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] += (double)run[k];
-    block_reduce_k<9>(acc, red, tot);
-    if (threadIdx.x < 8 && i0 + threadIdx.x / 2 < nv) pb[2 * i0 + threadIdx.x] = tot[threadIdx.x];
-    if (threadIdx.x == 8 && i0 == 0) pb[2 * nv] = tot[8];
+    for (int q = 0; q < NW; ++q) s += wsum[k][q];
+    pb[k] = s;
   }
   __threadfence();
   __syncthreads();
@@ -108,13 +142,15 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
   if (threadIdx.x == 0) counter[b] = 0;
 }
 
+// w -= sum_i h_i v_i over the tile held in registers, and ||w||^2.
 template <typename R>
-__global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V, long long vinst, long long U,
+__global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V, long long vinst, long long Us,
                                                int nv, int wi, const double *__restrict__ h, int hstride,
                                                const int *__restrict__ act, const int *__restrict__ gate,
                                                double *partial, unsigned *counter, double *wn_out,
                                                int *gate_out, int force) {
   using C = typename Cx<R>::T;
+  constexpr int EPT = Ept<R>::v;
   __shared__ C hs[MAXM + 1];
   __shared__ double red[32];
   const int b = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
@@ -124,29 +160,31 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
     hs[i] = mk((R)h[(long long)b * hstride + 2 * i], (R)h[(long long)b * hstride + 2 * i + 1]);
   __syncthreads();
   C *Vb = V + b * vinst;
-  C *W = Vb + (long long)wi * U;
-  const long long chunk = (U + nblk - 1) / nblk;
-  const long long e0 = blk * chunk, e1 = min(U, e0 + chunk);
+  C *W = Vb + (long long)wi * Us;
+  const long long ntiles = (Us + KT * EPT - 1) / (KT * EPT);
   double acc = 0;
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    C w = W[e];
-    int i = 0;
-    for (; i + 4 <= nv; i += 4) {
-      C v0 = Vb[(long long)i * U + e], v1 = Vb[(long long)(i + 1) * U + e];
-      C v2 = Vb[(long long)(i + 2) * U + e], v3 = Vb[(long long)(i + 3) * U + e];
-      w = csub(w, cmul(hs[i], v0));
-      w = csub(w, cmul(hs[i + 1], v1));
-      w = csub(w, cmul(hs[i + 2], v2));
-      w = csub(w, cmul(hs[i + 3], v3));
+  for (long long t = blk; t < ntiles; t += nblk) {
+    const long long e0 = t * (KT * EPT) + (long long)threadIdx.x * EPT;
+    if (e0 >= Us) continue;
+    C w[EPT];
+    load_ept<C, EPT>(w, W + e0);
+    for (int i = 0; i < nv; ++i) {
+      C v[EPT];
+      load_ept<C, EPT>(v, Vb + (long long)i * Us + e0);
+      const C hi = hs[i];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) w[k] = csub(w[k], cmul(hi, v[k]));
     }
-    for (; i < nv; ++i) w = csub(w, cmul(hs[i], Vb[(long long)i * U + e]));
-    W[e] = w;
-    acc += (double)w.x * w.x + (double)w.y * w.y;
+    store_ept<C, EPT>(W + e0, w);
+    R n2 = 0;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) n2 += w[k].x * w[k].x + w[k].y * w[k].y;
+    acc += (double)n2;
   }
   if (last_block_sum(acc, red, partial, counter, wn_out, b, nblk, blk)) {
     if (gate_out && threadIdx.x == 0) {
       const double before = h[(long long)b * hstride + 2 * nv];
-      gate_out[b] = (force || wn_out[b] < 0.5 * before) ? 1 : 0;
+      gate_out[b] = (force == 1 || (force == 0 && wn_out[b] < 0.5 * before)) ? 1 : 0;
     }
   }
 }
@@ -227,7 +265,7 @@ __global__ void k_backsolve(KrylovPtrs k) {
 template <typename R>
 __global__ void __launch_bounds__(KT) k_sol_update(double2 *__restrict__ x64, long long xinst,
                                                    const typename Cx<R>::T *__restrict__ V, long long vinst,
-                                                   long long U, const double2 *__restrict__ y, int m,
+                                                   long long U, long long Us, const double2 *__restrict__ y, int m,
                                                    const int *__restrict__ kcount, const int *__restrict__ need) {
   using C = typename Cx<R>::T;
   __shared__ C ys[MAXM];
@@ -241,11 +279,31 @@ __global__ void __launch_bounds__(KT) k_sol_update(double2 *__restrict__ x64, lo
   double2 *xb = x64 + b * xinst;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < U; e += (long long)gridDim.x * blockDim.x) {
     C d = mk((R)0, (R)0);
-    for (int i = 0; i < n; ++i) d = cadd(d, cmul(ys[i], Vb[(long long)i * U + e]));
+    for (int i = 0; i < n; ++i) d = cadd(d, cmul(ys[i], Vb[(long long)i * Us + e]));
     double2 xv = xb[e];
     xb[e] = mk(xv.x + (double)d.x, xv.y + (double)d.y);
   }
 }
+
+// zero the padding (U..Us) of every stored Krylov vector
+template <typename C>
+__global__ void k_zero_pads(C *V, long long nvec, long long U, long long Us) {
+  const long long pad = Us - U, tot = nvec * pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long v = e / pad;
+    V[v * Us + U + (e - v * pad)] = mk((decltype(V[0].x))0, (decltype(V[0].x))0);
+  }
+}
+
+template <typename C>
+cudaError_t launch_zero_pads(C *V, long long nvec, long long U, long long Us, cudaStream_t st) {
+  if (Us == U || nvec == 0) return cudaSuccess;
+  const long long tot = nvec * (Us - U);
+  k_zero_pads<<<(int)std::min<long long>((tot + 255) / 256, 1184), 256, 0, st>>>(V, nvec, U, Us);
+  return cudaGetLastError();
+}
+template cudaError_t launch_zero_pads<float2>(float2 *, long long, long long, long long, cudaStream_t);
+template cudaError_t launch_zero_pads<double2>(double2 *, long long, long long, long long, cudaStream_t);
 
 __global__ void k_set_rhs(double2 *r64, long long xinst, Geo g, const Inst *inst, int B) {
   const long long tot = (long long)B * g.U;
@@ -273,19 +331,19 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
                                  Profiler *prof) {
   const int nv = j + 1, wi = j + 1, hs = 2 * (k.m + 1) + 1;
   dim3 grid(k.nblk, k.B);
-  const double vb = (double)sizeof(typename Cx<R>::T) * k.U * k.B;
+  const double vb = (double)sizeof(typename Cx<R>::T) * k.U * k.B;  // logical bytes per vector batch
   if (prof) prof->begin(KIND_DOTS, st);
-  k_dots<R><<<grid, KT, 0, st>>>(V, vinst, k.U, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs);
+  k_dots<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
-  k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.U, nv, wi, k.hdot0, hs, k.act, nullptr, k.partial, k.counter, k.wn0,
+  k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot0, hs, k.act, nullptr, k.partial, k.counter, k.wn0,
                                    k.gate, k.force_reorth);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   if (prof) prof->begin(KIND_DOTS, st);
-  k_dots<R><<<grid, KT, 0, st>>>(V, vinst, k.U, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs);
+  k_dots<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs);
   if (prof) prof->end(KIND_DOTS, st, 0.0);
   if (prof) prof->begin(KIND_UPDATE, st);
-  k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.U, nv, wi, k.hdot1, hs, k.act, k.gate, k.partial, k.counter, k.wn1,
+  k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot1, hs, k.act, k.gate, k.partial, k.counter, k.wn1,
                                    nullptr, 0);
   if (prof) prof->end(KIND_UPDATE, st, 0.0);
   return cudaGetLastError();
@@ -306,7 +364,7 @@ cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst
                               long long vinst, const int *need, cudaStream_t st, Profiler *prof) {
   dim3 grid(k.nblk, k.B);
   if (prof) prof->begin(KIND_OTHER, st);
-  k_sol_update<R><<<grid, KT, 0, st>>>(x64, xinst, V, vinst, k.U, k.y, k.m, k.kcount, need);
+  k_sol_update<R><<<grid, KT, 0, st>>>(x64, xinst, V, vinst, k.U, k.Us, k.y, k.m, k.kcount, need);
   if (prof) prof->end(KIND_OTHER, st, 0.0);
   return cudaGetLastError();
 }

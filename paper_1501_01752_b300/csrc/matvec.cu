@@ -28,7 +28,7 @@ template <typename C> __device__ __forceinline__ C czero() { C z; z.x = 0; z.y =
 
 // ---------------------------------------------------------------- pass 1
 template <typename R, bool ADJ>
-__global__ void __launch_bounds__(256) k_fwd_x(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
                         typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale, int write_back,
                         const int *__restrict__ act, const Inst *__restrict__ inst,
                         const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg, int rows,
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geo g, typename Cx<R>::T *__restr
 
 // ---------------------------------------------------------------- pass 2
 template <typename R>
-__global__ void __launch_bounds__(256) k_yz(Geo g, typename Cx<R>::T *__restrict__ T, const R *__restrict__ D,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_yz(Geo g, typename Cx<R>::T *__restrict__ T, const R *__restrict__ D,
                      const int *__restrict__ act, const typename Cx<R>::T *__restrict__ twg) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -145,11 +145,12 @@ __global__ void __launch_bounds__(256) k_yz(Geo g, typename Cx<R>::T *__restrict
 }
 
 // ---------------------------------------------------------------- pass 3
-// MODE 0: Y = X - G u     (forward operator)
-// MODE 1: Y = b - (X - G u), with b = a at m = 0 (residual of Eq. 4)
-// MODE 2: Y = X - u       (adjoint: G was applied in pass 1)
+// MODE 0: Y = X - G u          (forward operator)
+// MODE 1: Y = b - (X - G u)    (residual of Eq. 4; b = a at m = 0)
+// MODE 2: Y = X - u            (adjoint operator: G was applied in pass 1)
+// MODE 3: Y = b - (X - u)      (residual of the adjoint system)
 template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_inv_x(Geo g, const typename Cx<R>::T *__restrict__ T, const typename Cx<R>::T *__restrict__ X,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, const typename Cx<R>::T *__restrict__ T, const typename Cx<R>::T *__restrict__ X,
                         long long xstride, typename Cx<R>::T *__restrict__ Y, long long ystride,
                         const int *__restrict__ act, const Inst *__restrict__ inst, const R *__restrict__ iden,
                         const typename Cx<R>::T *__restrict__ twg, int rows, int nchunk, double *partial,
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(256) k_inv_x(Geo g, const typename Cx<R>::T *_
       const int rx = e / nr, row = e - rx * nr;
       S[(c * rows + row) * P0 + rx] = Tb[(((long long)rx * 3 + c) * N2 + mz) * N1 + my0 + row];
     }
-  if (MODE != 2) {
+  if (!(MODE & 2)) {
     for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (R)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
     for (int i = threadIdx.x; i < nr; i += blockDim.x) kys[i] = (R)(inst[b].kinc[1] + (my0 + i - g.n[1]) * g.K[1]);
   }
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(256) k_inv_x(Geo g, const typename Cx<R>::T *_
     const long long h = ((long long)mz * N1 + my0 + row) * N0 + mx;
     const int px = wrap(mx, g.n[0], L0);
     C u0 = S[(0 * rows + row) * P0 + px], u1 = S[(1 * rows + row) * P0 + px], u2 = S[(2 * rows + row) * P0 + px];
-    if (MODE != 2) {
+    if (!(MODE & 2)) {
       const R kx = kxs[mx], ky = kys[row], id = iden[b * Nh + h];
       const C ku = mk(kx * u0.x + ky * u1.x + kz * u2.x, kx * u0.y + ky * u1.y + kz * u2.y);
       u0 = mk(id * (kb2 * u0.x - kx * ku.x), id * (kb2 * u0.y - kx * ku.y));
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256) k_inv_x(Geo g, const typename Cx<R>::T *_
       u2 = mk(id * (kb2 * u2.x - kz * ku.x), id * (kb2 * u2.y - kz * ku.y));
     }
     C y0 = csub(Xb[h], u0), y1 = csub(Xb[Nh + h], u1), y2 = csub(Xb[2 * Nh + h], u2);
-    if (MODE == 1) {
+    if (MODE & 1) {
       C b0 = czero<C>(), b1 = czero<C>(), b2 = czero<C>();
       if (h == h0) {
         b0 = mk((R)inst[b].a[0], (R)inst[b].a[1]);
@@ -283,7 +284,7 @@ cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *pro
     const size_t smem = cs * (TWN + (size_t)rows * (g.L[0] + 1));
     dim3 grid(g.N[2] * nchunk, a.B);
     if (prof) prof->begin(KIND_FWD_X, st);
-    if (a.mode == 2) {
+    if (a.mode & 2) {
       cudaFuncSetAttribute(k_fwd_x<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fwd_x<R, true><<<grid, threads, smem, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
                                                   a.iden, a.tw, rows, nchunk);
@@ -320,11 +321,12 @@ cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *pro
                                              rows, nchunk, a.partial, a.counter, a.norm_out)
     if (a.mode == 0) { GSM_P3(0); }
     else if (a.mode == 1) { GSM_P3(1); }
-    else { GSM_P3(2); }
+    else if (a.mode == 2) { GSM_P3(2); }
+    else { GSM_P3(3); }
 #undef GSM_P3
     if (prof)
       prof->end(KIND_INV_X, st,
-                (double)a.B * (cs * (double)(g.Tsz + 2 * g.U) + (a.mode != 2 ? sizeof(R) * (double)g.Nh : 0.0)));
+                (double)a.B * (cs * (double)(g.Tsz + 2 * g.U) + (!(a.mode & 2) ? sizeof(R) * (double)g.Nh : 0.0)));
   }
   return cudaGetLastError();
 }

@@ -69,16 +69,23 @@ def layered_stack(period=0.3, d1_frac=0.5, eps1=1.0, eps2=4.0, axis=2):
     return dict(periods=(L, L, L), eps_host=eps1, shapes=[(BOX, tuple(center), tuple(size), eps2)])
 
 
-def random_binary_voxels(M=64, seed=1501, sigma=2.0, fill=0.3, eps=(1.0, 6.0)):
+def random_binary_voxels(M=64, seed=1501, sigma=2.0, fill=0.3, eps=(1.0, 6.0), mirror=False):
     """Seeded Gaussian-smoothed random binary field on an M^3 grid: iid
     N(0, 1) (numpy PCG64), periodic Gaussian smoothing of sigma voxels,
-    threshold at the (1 - fill) quantile.  Returns eps[v_z, v_y, v_x]."""
+    threshold at the (1 - fill) quantile.  mirror=True averages the smoothed
+    field over the mirrors x, y, z -> -x, -y, -z about the cell centre before
+    thresholding, so the cell has orthorhombic symmetry and principal axes
+    along x, y, z.  Returns eps[v_z, v_y, v_x]."""
     rng = np.random.Generator(np.random.PCG64(seed))
     g = rng.standard_normal((M, M, M))
     f = np.fft.fftfreq(M)
     fz, fy, fx = np.meshgrid(f, f, f, indexing="ij")
     kernel = np.exp(-2.0 * (math.pi * sigma) ** 2 * (fx**2 + fy**2 + fz**2))
     s = np.fft.ifftn(np.fft.fftn(g) * kernel).real
+    if mirror:
+        s = s + s[::-1, :, :]
+        s = s + s[:, ::-1, :]
+        s = s + s[:, :, ::-1]
     thr = np.quantile(s, 1.0 - fill)
     return np.where(s > thr, eps[1], eps[0]).astype(np.float64)
 
