@@ -7,6 +7,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -34,6 +35,7 @@ struct Level {
   Geo g;
   double *D64 = nullptr;
   float *D32 = nullptr;
+  float *D32p = nullptr;   // D in the register-FFT order (FFT sizes 32/64 only)
 };
 
 // Device workspace for one level, sized for B instances and a basis of m+1.
@@ -78,6 +80,7 @@ struct gsm_plan_s {
   float2 *tw32 = nullptr;
   Profiler prof;
   long long launches = 0;  // kernels issued by this plan
+  bool team_only = false;  // GSM_FFT_PATH=team: shared-memory FFTs everywhere
   // pinned host staging
   char *pin = nullptr;
   size_t pin_bytes = 0;
@@ -190,7 +193,7 @@ static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nbl
   w.iden32 = (float *)take((size_t)B * g.Nh * 4);
   w.inst = (Inst *)take((size_t)B * sizeof(Inst));
   w.need = (int *)take((size_t)B * 4);
-  const int mvb = std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8));
+  const int mvb = std::max(std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8)), matvec_reg_blocks_pass3(g));
   w.mv_partial = (double *)take((size_t)B * mvb * 8);
   w.mv_norm = (double *)take((size_t)B * 8);
   w.mv_counter = (unsigned *)take((size_t)B * 4);
@@ -303,6 +306,10 @@ static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
   CK(cudaMemcpyAsync(dc, grid.data(), LL * sizeof(double2), cudaMemcpyHostToDevice, p->st));
   for (int a = 0; a < 3; ++a) CK(launch_fft_axis(dc, g.L[0], g.L[1], g.L[2], a, +1, 1, 0, p->tw64, p->st));
   CK(launch_d_finalize(dc, g, 1.0 / (double)LL, lv.D64, lv.D32, p->st));
+  if (reg_path_ok(g)) {
+    if (!lv.D32p) CK(cudaMalloc(&lv.D32p, LL * sizeof(float)));
+    CK(launch_d_permute(g, lv.D32, lv.D32p, p->st));
+  }
   CK(cudaStreamSynchronize(p->st));
   cudaFree(dc);
   *out = &lv;
@@ -336,6 +343,17 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
         kmax2 = std::max(kmax2, k2);
       }
   return GSM_OK;
+}
+
+// Matrix-vector product in the working precision: the register-FFT kernels
+// for complex64 with FFT sizes 32/64 (forward and residual forms), the
+// shared-memory FFT kernels otherwise.
+template <typename R>
+static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a, Profiler *prof) {
+  if constexpr (sizeof(R) == 4) {
+    if (!p->team_only && a.mode < 2 && lv.D32p && reg_path_ok(a.g)) return launch_matvec_reg(a, lv.D32p, p->st, prof);
+  }
+  return launch_matvec<R>(a, p->st, prof);
 }
 
 // ------------------------------------------------------------------ solve
@@ -465,7 +483,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       if (!live) break;
       mv.X = V + (long long)j * Us;
       mv.Y = V + (long long)(j + 1) * Us;
-      CK(launch_matvec<R>(mv, st, prof));
+      CK(matvec<R>(p, lv, mv, prof));
       CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
       CK(launch_finish(k, j, st));
       p->launches += 3 + 4 + 1;
@@ -606,6 +624,10 @@ gsm_status gsm_plan(const gsm_plan_desc *desc, gsm_plan_t **out) {
     return GSM_ERR_CUDA;
   }
   p->st = (cudaStream_t)desc->cuda_stream;
+  {
+    const char *fp = std::getenv("GSM_FFT_PATH");
+    p->team_only = fp && std::strcmp(fp, "team") == 0;
+  }
   std::vector<double2> t64(TWN_HOST);
   std::vector<float2> t32(TWN_HOST);
   for (int j = 0; j < TWN_HOST; ++j) {
@@ -634,6 +656,7 @@ void gsm_plan_destroy(gsm_plan_t *p) {
   for (auto &kv : p->levels) {
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
+    cudaFree(kv.second.D32p);
   }
   for (auto &kv : p->works) cudaFree(kv.second.base);
   cudaFree(p->tw64);
@@ -677,8 +700,10 @@ gsm_status gsm_set_permittivity(gsm_plan_t *p, const double eps_host[2], const g
   for (auto &kv : p->levels) {
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
+    cudaFree(kv.second.D32p);
     kv.second.D64 = nullptr;
     kv.second.D32 = nullptr;
+    kv.second.D32p = nullptr;
   }
   Level *lv;
   return get_level(p, p->d.n_harm, &lv);
@@ -730,7 +755,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.iden = w->iden32;
     a.tw = p->tw32;
     a.mode = adjoint ? 2 : 0;
-    CK(launch_matvec<float>(a, st, nullptr));
+    CK(matvec<float>(p, *lv, a, nullptr));
     CK(launch_convert_f2d(yf, yd, (long long)n * g.U, st));
   } else {
     MatvecArgs<double> a;

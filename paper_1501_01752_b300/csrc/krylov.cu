@@ -97,7 +97,37 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
     for (int k = 0; k < EPT; ++k) n2 += w[k].x * w[k].x + w[k].y * w[k].y;
     n2 = warp_sum(n2);
     if (lane == 0) wsum[2 * nv][warp] += (double)n2;
-    for (int i = 0; i < nv; ++i) {
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {   // four basis vectors in flight per thread
+      C v[4][EPT];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (ok) load_ept<C, EPT>(v[u], Vb + (long long)(i + u) * Us + e0);
+        else
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) v[u][k] = mk((R)0, (R)0);
+      }
+      R d[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        R re = 0, im = 0;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          re += v[u][k].x * w[k].x + v[u][k].y * w[k].y;   // conj(v) w
+          im += v[u][k].x * w[k].y - v[u][k].y * w[k].x;
+        }
+        d[2 * u] = re;
+        d[2 * u + 1] = im;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) d[u] += __shfl_xor_sync(0xffffffffu, d[u], o);
+      if (lane == 0)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) wsum[2 * i + u][warp] += (double)d[u];
+    }
+    for (; i < nv; ++i) {
       C v[EPT];
       if (ok) load_ept<C, EPT>(v, Vb + (long long)i * Us + e0);
       else
@@ -106,7 +136,7 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
       R re = 0, im = 0;
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
-        re += v[k].x * w[k].x + v[k].y * w[k].y;   // conj(v) w
+        re += v[k].x * w[k].x + v[k].y * w[k].y;
         im += v[k].x * w[k].y - v[k].y * w[k].x;
       }
       re = warp_sum(re);
@@ -168,7 +198,19 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
     if (e0 >= Us) continue;
     C w[EPT];
     load_ept<C, EPT>(w, W + e0);
-    for (int i = 0; i < nv; ++i) {
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {
+      C v[4][EPT];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_ept<C, EPT>(v[u], Vb + (long long)(i + u) * Us + e0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const C hi = hs[i + u];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) w[k] = csub(w[k], cmul(hi, v[u][k]));
+      }
+    }
+    for (; i < nv; ++i) {
       C v[EPT];
       load_ept<C, EPT>(v, Vb + (long long)i * Us + e0);
       const C hi = hs[i];

@@ -22,6 +22,10 @@ CASES = [
      [wl.point(0.8 * K0), wl.point(0.75 * K0, (0, 0, 1), (0, 1, 0)), wl.point(0.9 * K0, (0.6, 0, 0.8), (0, 1, 0))]),
     ("ellipsoid_21", wl.ellipsoid_lattice(), (21, 21, 21), 1.0, [wl.point(0.83 * K0)]),
     ("woodpile_31", wl.woodpile(), (31, 31, 31), 1.0, [wl.point(0.8 * K0), wl.point(0.7 * K0, (0, 0, 1), (0, 1, 0))]),
+    # mixed FFT sizes 32/64 per axis (register-FFT path with unequal axes)
+    ("random_15_21_31", wl.random_shapes(4, period=(0.3, 0.32, 0.34)), (15, 21, 31), 1.0,
+     [wl.point(0.77 * K0, (0.2, 0.3, 0.9), (1, 0, 0.1))]),
+    ("random_21_15_15", wl.random_shapes(5), (21, 15, 15), 1.0, [wl.point(0.8 * K0)]),
 ]
 
 
@@ -33,8 +37,13 @@ def _oracle_apply(st, n_harm, eps_b, pt, x, adjoint):
     return A.adjoint(x) if adjoint else A(x)
 
 
+@pytest.mark.parametrize("path", ["auto", "team"])
 @pytest.mark.parametrize("name,st,n_harm,eps_b,points", CASES, ids=[c[0] for c in CASES])
-def test_apply_matches_oracle(name, st, n_harm, eps_b, points):
+def test_apply_matches_oracle(name, st, n_harm, eps_b, points, path, monkeypatch):
+    # "auto" takes the register-FFT kernels for complex64 when every FFT size is
+    # 32 or 64; "team" forces the shared-memory FFT kernels everywhere
+    if path == "team":
+        monkeypatch.setenv("GSM_FFT_PATH", "team")
     g = gsm()
     x = wl.random_field(n_harm, 100 + len(name), batch=len(points))
     plan = g.plan_for(st, n_harm, eps_b=eps_b, precision=g.FP64)
