@@ -35,7 +35,6 @@ struct Level {
   Geo g;
   double *D64 = nullptr;
   float *D32 = nullptr;
-  float *D32p = nullptr;   // D in the register-FFT order (FFT sizes 32/64 only)
 };
 
 // Device workspace for one level, sized for B instances and a basis of m+1.
@@ -306,10 +305,6 @@ static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
   CK(cudaMemcpyAsync(dc, grid.data(), LL * sizeof(double2), cudaMemcpyHostToDevice, p->st));
   for (int a = 0; a < 3; ++a) CK(launch_fft_axis(dc, g.L[0], g.L[1], g.L[2], a, +1, 1, 0, p->tw64, p->st));
   CK(launch_d_finalize(dc, g, 1.0 / (double)LL, lv.D64, lv.D32, p->st));
-  if (reg_path_ok(g)) {
-    if (!lv.D32p) CK(cudaMalloc(&lv.D32p, LL * sizeof(float)));
-    CK(launch_d_permute(g, lv.D32, lv.D32p, p->st));
-  }
   CK(cudaStreamSynchronize(p->st));
   cudaFree(dc);
   *out = &lv;
@@ -345,13 +340,13 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
   return GSM_OK;
 }
 
-// Matrix-vector product in the working precision: the register-FFT kernels
+// Matrix-vector product in the working precision: the lane-team FFT kernels
 // for complex64 with FFT sizes 32/64 (forward and residual forms), the
-// shared-memory FFT kernels otherwise.
+// generic shared-memory FFT kernels otherwise.
 template <typename R>
 static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a, Profiler *prof) {
   if constexpr (sizeof(R) == 4) {
-    if (!p->team_only && a.mode < 2 && lv.D32p && reg_path_ok(a.g)) return launch_matvec_reg(a, lv.D32p, p->st, prof);
+    if (!p->team_only && a.mode < 2 && reg_path_ok(a.g)) return launch_matvec_reg(a, p->st, prof);
   }
   return launch_matvec<R>(a, p->st, prof);
 }
@@ -656,7 +651,6 @@ void gsm_plan_destroy(gsm_plan_t *p) {
   for (auto &kv : p->levels) {
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
-    cudaFree(kv.second.D32p);
   }
   for (auto &kv : p->works) cudaFree(kv.second.base);
   cudaFree(p->tw64);
@@ -700,10 +694,8 @@ gsm_status gsm_set_permittivity(gsm_plan_t *p, const double eps_host[2], const g
   for (auto &kv : p->levels) {
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
-    cudaFree(kv.second.D32p);
     kv.second.D64 = nullptr;
     kv.second.D32 = nullptr;
-    kv.second.D32p = nullptr;
   }
   Level *lv;
   return get_level(p, p->d.n_harm, &lv);

@@ -66,20 +66,23 @@ template <typename R> __device__ __forceinline__ R warp_sum(R v) {
 // every basis vector streamed once.  Products are summed in the basis
 // precision over one tile (EPT per thread, then a 32-lane tree) and the tile
 // sums are accumulated in FP64.
+constexpr int GV = 8;  // basis vectors per block of k_dots (grid.x = tile blocks x vector groups)
+
 template <typename R>
 __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict__ V, long long vinst, long long Us,
                                              int nv, int wi, const int *__restrict__ act,
                                              const int *__restrict__ gate, double *partial, unsigned *counter,
-                                             double *out, int ostride) {
+                                             double *out, int ostride, int nblk) {
   using C = typename Cx<R>::T;
   constexpr int EPT = Ept<R>::v, NW = KT / 32;
-  __shared__ double wsum[2 * MAXM + 3][NW];
+  __shared__ double wsum[2 * GV + 1][NW];
   __shared__ int am_last;
-  const int b = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
+  const int b = blockIdx.y, blk = blockIdx.x % nblk, grp = blockIdx.x / nblk;
   if (!act[b]) return;
   if (gate && !gate[b]) return;
   const int K = 2 * nv + 1, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = threadIdx.x; k < K * NW; k += blockDim.x) (&wsum[0][0])[k] = 0.0;
+  const int i0 = grp * GV, i1 = min(nv, i0 + GV), ng = i1 - i0;
+  for (int k = threadIdx.x; k < (2 * GV + 1) * NW; k += blockDim.x) (&wsum[0][0])[k] = 0.0;
   __syncthreads();
   const C *Vb = V + b * vinst;
   const C *W = Vb + (long long)wi * Us;
@@ -92,17 +95,19 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
     else
 #pragma unroll
       for (int k = 0; k < EPT; ++k) w[k] = mk((R)0, (R)0);
-    R n2 = 0;
+    if (grp == 0) {
+      R n2 = 0;
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) n2 += w[k].x * w[k].x + w[k].y * w[k].y;
-    n2 = warp_sum(n2);
-    if (lane == 0) wsum[2 * nv][warp] += (double)n2;
+      for (int k = 0; k < EPT; ++k) n2 += w[k].x * w[k].x + w[k].y * w[k].y;
+      n2 = warp_sum(n2);
+      if (lane == 0) wsum[2 * GV][warp] += (double)n2;
+    }
     int i = 0;
-    for (; i + 4 <= nv; i += 4) {   // four basis vectors in flight per thread
+    for (; i + 4 <= ng; i += 4) {   // four basis vectors in flight per thread
       C v[4][EPT];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (ok) load_ept<C, EPT>(v[u], Vb + (long long)(i + u) * Us + e0);
+        if (ok) load_ept<C, EPT>(v[u], Vb + (long long)(i0 + i + u) * Us + e0);
         else
 #pragma unroll
           for (int k = 0; k < EPT; ++k) v[u][k] = mk((R)0, (R)0);
@@ -127,9 +132,9 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
 #pragma unroll
         for (int u = 0; u < 8; ++u) wsum[2 * i + u][warp] += (double)d[u];
     }
-    for (; i < nv; ++i) {
+    for (; i < ng; ++i) {
       C v[EPT];
-      if (ok) load_ept<C, EPT>(v, Vb + (long long)i * Us + e0);
+      if (ok) load_ept<C, EPT>(v, Vb + (long long)(i0 + i) * Us + e0);
       else
 #pragma unroll
         for (int k = 0; k < EPT; ++k) v[k] = mk((R)0, (R)0);
@@ -148,18 +153,20 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
     }
   }
   __syncthreads();
+  // this block's share: dots i0..i1-1 (and ||w||^2 from group 0)
   double *pb = partial + ((long long)b * nblk + blk) * K;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+  for (int k = threadIdx.x; k < 2 * ng + (grp == 0); k += blockDim.x) {
+    const int src = k < 2 * ng ? k : 2 * GV;
     double s = 0;
 #pragma unroll
-    for (int q = 0; q < NW; ++q) s += wsum[k][q];
-    pb[k] = s;
+    for (int q = 0; q < NW; ++q) s += wsum[src][q];
+    pb[k < 2 * ng ? 2 * i0 + k : 2 * nv] = s;
+    __threadfence();
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned t = atomicAdd(&counter[b], 1u);
-    am_last = (t == (unsigned)nblk - 1);
+    am_last = (t == (unsigned)gridDim.x - 1);
   }
   __syncthreads();
   if (!am_last) return;
@@ -373,16 +380,17 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
                                  Profiler *prof) {
   const int nv = j + 1, wi = j + 1, hs = 2 * (k.m + 1) + 1;
   dim3 grid(k.nblk, k.B);
+  dim3 gdots(k.nblk * ((nv + GV - 1) / GV), k.B);
   const double vb = (double)sizeof(typename Cx<R>::T) * k.U * k.B;  // logical bytes per vector batch
   if (prof) prof->begin(KIND_DOTS, st);
-  k_dots<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs);
+  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs, k.nblk);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot0, hs, k.act, nullptr, k.partial, k.counter, k.wn0,
                                    k.gate, k.force_reorth);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   if (prof) prof->begin(KIND_DOTS, st);
-  k_dots<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs);
+  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs, k.nblk);
   if (prof) prof->end(KIND_DOTS, st, 0.0);
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot1, hs, k.act, k.gate, k.partial, k.counter, k.wn1,
