@@ -186,6 +186,23 @@ gsm_status gsm_profile(gsm_plan_t *plan, int enable);
 gsm_status gsm_profile_get(gsm_plan_t *plan, int kind, long long *launches,
                            double *total_ms, double *bytes);
 
+/* y = A x (Eq. 4 operator, FP64 kernels) for ONE point at the plan's full
+ * truncation, without allocating anything.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc during a
+ * solve step -- host applications whose own allocator has reserved the
+ * device memory up front, or latency-critical loops in which the implicit
+ * synchronisation of an allocation is not acceptable.  x and y are device
+ * pointers to 3 N^3 complex128 (y must not alias x).  Every temporary lives
+ * in one fixed device array of 8 MiB that the library holds on each GPU
+ * until the process exits; truncations whose temporaries (3 L_x N_y N_z
+ * complex128 plus 12 N^3 bytes) exceed it return GSM_ERR_ARG.  The first
+ * call on a device looks up that array's device address (once per device),
+ * so make the first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other plans) race and
+ * must be serialised by the caller.  The plan must have its permittivity
+ * set; the call synchronises the plan's stream. */
+gsm_status gsm_apply_noalloc(gsm_plan_t *plan, const gsm_point *point, const double *x, double *y);
+
 const char *gsm_last_error(const gsm_plan_t *plan);
 const char *gsm_version(void);
 

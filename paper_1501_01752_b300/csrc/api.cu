@@ -1043,3 +1043,24 @@ extern "C" gsm_status gsm_retrieve_tensor_grad(gsm_plan_t *p, double k0, const d
   if (gp.empty()) return GSM_OK;
   return adjoint_impl(p, (int)gp.size(), gp.data(), g6.data(), grad_voxel);
 }
+
+// ------------------------------------------------ internal accessors
+namespace gsm {
+// The plan's full-truncation level if it is already built (no allocation).
+gsm_status plan_full_level(gsm_plan_t *p, PlanView *v) {
+  if (!p) return GSM_ERR_ARG;
+  if (!p->have_eps) return fail(p, GSM_ERR_STATE, "gsm_set_permittivity has not been called");
+  Key key{{p->d.n_harm[0], p->d.n_harm[1], p->d.n_harm[2]}};
+  auto it = p->levels.find(key);
+  if (it == p->levels.end() || !it->second.D64) return fail(p, GSM_ERR_STATE, "the plan's truncation level is not built");
+  v->g = it->second.g;
+  v->D64 = it->second.D64;
+  v->tw64 = p->tw64;
+  v->st = p->st;
+  v->device = p->d.device;
+  return GSM_OK;
+}
+gsm_status plan_point(gsm_plan_t *p, const gsm_point &pt, const Geo &g, Inst &I) { return make_inst(p, pt, g, I); }
+gsm_status plan_fail(gsm_plan_t *p, gsm_status s, const char *msg) { return fail(p, s, msg); }
+void plan_count_launches(gsm_plan_t *p, int n) { p->launches += n; }
+}  // namespace gsm

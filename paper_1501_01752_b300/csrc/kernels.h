@@ -151,4 +151,13 @@ cudaError_t launch_adj_accum(const double2 *grid, long long LL, double2 *P, cuda
 cudaError_t launch_adj_fold(const double2 *P, const Geo &g, const int M[3], double2 *Q, cudaStream_t st);
 cudaError_t launch_adj_real(const double2 *Q, long long n, double scale, double *out, cudaStream_t st);
 
+// read-only view of a plan for entry points outside api.cu
+struct PlanView {
+  Geo g;
+  const double *D64;
+  const double2 *tw64;
+  cudaStream_t st;
+  int device;
+};
+
 }  // namespace gsm

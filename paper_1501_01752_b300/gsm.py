@@ -66,6 +66,7 @@ def _load():
         "gsm_plan_destroy": (None, [P]),
         "gsm_set_permittivity": (ct.c_int, [P, dp, ct.POINTER(Shape), ct.c_int, dp, ct.POINTER(ct.c_int)]),
         "gsm_apply": (ct.c_int, [P, ct.c_int, ct.POINTER(Point), P, P, ct.c_int, ct.c_int, ct.c_int]),
+        "gsm_apply_noalloc": (ct.c_int, [P, ct.POINTER(Point), P, P]),
         "gsm_solve": (ct.c_int, [P, ct.c_int, ct.POINTER(Point), P, ct.c_int, ct.POINTER(Info)]),
         "gsm_sweep": (ct.c_int, [P, ct.c_int, ct.POINTER(Point), dp, ct.POINTER(Info)]),
         "gsm_fit_poles": (ct.c_int, [ct.c_int, dp, dp, ct.c_int, ct.c_int, dp, dp]),
@@ -227,6 +228,14 @@ class Plan:
             s = lib.gsm_apply(self.h, len(points), pts, ct.c_void_p(xin.ctypes.data), ct.c_void_p(y.ctypes.data), 0,
                               precision, int(adjoint))
         self._check(s, "gsm_apply")
+        return y
+
+    def apply_noalloc(self, point, x, y):
+        """y = A x for one point with the fixed-scratch FP64 product
+        (gsm_apply_noalloc); x and y are torch CUDA complex128 tensors."""
+        pts = make_points([point])
+        s = lib.gsm_apply_noalloc(self.h, pts, ct.c_void_p(x.data_ptr()), ct.c_void_p(y.data_ptr()))
+        self._check(s, "gsm_apply_noalloc")
         return y
 
     def solve(self, points, out=None):
