@@ -3,7 +3,8 @@
 //
 // With j = t + TS a (t < TS, a < 8) and q = p + 8 s (p < 8, s < TS):
 //   X[q] = sum_t w_TS^{S t s} w_L^{S t p} sum_a x[t + TS a] w_8^{S a p}.
-// forward(): lane t holds x[t + TS a] in register a ("natural" layout);
+// forward(): lane t holds x[t + TS a] in register a ("natural" layout;
+//   registers 2..5 must be zero, which harmonic inputs with L >= 2N - 1 are);
 //   8-point DFT over a, twiddle w_L^{S t p}, transpose through the team
 //   buffer, TS-point DFTs over t.  Result: X[p + 8 s] in lane p (TS = 8,
 //   register s) or in lane p mod 4, register 4 (p / 4) + s (TS = 4)
@@ -38,9 +39,34 @@ template <int L> struct Team8 {
     return cmul(v, w);
   }
 
+  // 8-point DFT of inputs whose registers 2..5 are zero: a transform of
+  // harmonics m in [-n, n] placed at m mod L with L >= 4 n + 4 has nonzero
+  // inputs only at t + TS a for a in {0, 1, 6, 7}.
+  template <int S, typename C> __device__ static __forceinline__ void dft8_in0167(C *v) {
+    const C e0 = cadd(v[0], v[6]), e2 = csub(v[0], v[6]);
+    const C r6 = mul_si<S>(v[6]);
+    const C e1 = csub(v[0], r6), e3 = cadd(v[0], r6);
+    const C o0 = cadd(v[1], v[7]), o2 = csub(v[1], v[7]);
+    const C r7 = mul_si<S>(v[7]);
+    const C o1 = csub(v[1], r7), o3 = cadd(v[1], r7);
+    using R = decltype(o0.x);
+    const R h = (R)0.70710678118654752440;
+    const C t1 = mk((o1.x - S * o1.y) * h, (o1.y + S * o1.x) * h);
+    const C t2 = mul_si<S>(o2);
+    const C t3 = mk((-o3.x - S * o3.y) * h, (-o3.y + S * o3.x) * h);
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, t1);
+    v[5] = csub(e1, t1);
+    v[2] = cadd(e2, t2);
+    v[6] = csub(e2, t2);
+    v[3] = cadd(e3, t3);
+    v[7] = csub(e3, t3);
+  }
+
   template <int S, typename C>
   __device__ static __forceinline__ void forward(C (&v)[8], int lane, const C (&w)[8], C *buf, unsigned mask) {
-    dft8<S>(v);                                     // Y[t = lane][p], p = register
+    dft8_in0167<S>(v);                              // Y[t = lane][p], p = register
 #pragma unroll
     for (int p = 1; p < 8; ++p) v[p] = tmul<S>(v[p], w[p]);
 #pragma unroll

@@ -89,9 +89,9 @@ template <typename R> struct MatvecArgs {
 };
 
 template <typename R> cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof);
-// complex64 team-of-lanes FFT path for FFT sizes 32/64 on every axis (modes 0, 1)
+// team-of-lanes FFT path for FFT sizes 32/64 on every axis (modes 0, 1)
 bool reg_path_ok(const Geo &g);
-cudaError_t launch_matvec_reg(const MatvecArgs<float> &a, cudaStream_t st, Profiler *prof);
+template <typename R> cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof);
 int matvec_reg_blocks_pass3(const Geo &g);
 int matvec_blocks_pass3(const Geo &g, size_t csize);
 size_t matvec_max_smem(const Geo &g, size_t csize);

@@ -389,13 +389,14 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot0, hs, k.act, nullptr, k.partial, k.counter, k.wn0,
                                    k.gate, k.force_reorth);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
+  if (k.force_reorth == 2) return cudaGetLastError();   // no second pass: gate was cleared
   if (prof) prof->begin(KIND_DOTS, st);
   k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs, k.nblk);
-  if (prof) prof->end(KIND_DOTS, st, 0.0);
+  if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot1, hs, k.act, k.gate, k.partial, k.counter, k.wn1,
                                    nullptr, 0);
-  if (prof) prof->end(KIND_UPDATE, st, 0.0);
+  if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   return cudaGetLastError();
 }
 

@@ -1,4 +1,4 @@
-// Complex64 fast path of the Eq. 4 operator for FFT sizes 32 and 64 per
+// Lane-team path of the Eq. 4 operator (complex64 and complex128) for FFT sizes 32 and 64 per
 // axis: the same three passes as matvec.cu, with every 1D transform done by
 // a team of L/8 lanes holding 8 values each (fft_team8.cuh): one radix-8 DFT
 // in registers, one bank-conflict-free transpose through a team buffer, the
@@ -39,35 +39,36 @@ struct Lanes {
   }
 };
 
-template <int L0>
-__global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, float2 *__restrict__ X, long long xstride,
-                                                 float2 *__restrict__ T, const float *__restrict__ scale,
+template <typename R, int L0>
+__global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
+                                                 typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
                                                  int write_back, const int *__restrict__ act,
-                                                 const float2 *__restrict__ twg) {
+                                                 const typename Cx<R>::T *__restrict__ twg) {
+  using C = typename Cx<R>::T;
   using F = Team8<L0>;
   constexpr int TS = F::TS, RB = TT / TS;
-  __shared__ float2 tw[TWN];
-  __shared__ float2 bufs[RB * F::BUF];
+  __shared__ C tw[TWN];
+  __shared__ C bufs[RB * F::BUF];
   const int b = blockIdx.y;
   if (act && !act[b]) return;
   for (int i = threadIdx.x; i < TWN; i += blockDim.x) tw[i] = twg[i];
   __syncthreads();
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
   const Lanes ln(TS);
-  float2 w[8];
+  C w[8];
   F::twiddles(w, ln.lane, tw);
   const long long nrows = 3LL * N2 * N1;
   const long long r = (long long)blockIdx.x * RB + ln.team;
   const bool valid = r < nrows;
-  const float s = scale ? scale[b] : 1.f;
-  float2 *Xr = X + b * xstride + r * N0;
-  float2 v[8];
+  const R s = scale ? scale[b] : (R)1;
+  C *Xr = X + b * xstride + r * N0;
+  C v[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
-    v[a] = make_float2(0.f, 0.f);
+    v[a] = mk((R)0, (R)0);
     if (valid && h >= 0) {
-      float2 x = Xr[h];
+      C x = Xr[h];
       x.x *= s;
       x.y *= s;
       if (write_back) Xr[h] = x;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, float2 *__restrict__ X, 
   if (!valid) return;
   const int plane = (int)(r / N1), my = (int)(r - (long long)plane * N1);
   const int c = plane / N2, mz = plane - c * N2;
-  float2 *Tb = T + b * g.Tsz + (long long)mz * N1 + my;
+  C *Tb = T + b * g.Tsz + (long long)mz * N1 + my;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int rx = F::freq(ln.lane, q);
@@ -86,34 +87,36 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, float2 *__restrict__ X, 
   }
 }
 
-template <int LY, int LZ>
-__global__ void __launch_bounds__(TT) k_yz_t8(Geo g, float2 *__restrict__ T, const float *__restrict__ D,
-                                              const int *__restrict__ act, const float2 *__restrict__ twg) {
+template <typename R, int LY, int LZ>
+__global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restrict__ T, const R *__restrict__ D,
+                                              const int *__restrict__ act, const typename Cx<R>::T *__restrict__ twg) {
+  using C = typename Cx<R>::T;
   using FY = Team8<LY>;
   using FZ = Team8<LZ>;
   constexpr int NTY = TT / FY::TS, NTZ = TT / FZ::TS, NT = NTY > NTZ ? NTY : NTZ;
-  __shared__ float2 tw[TWN];
-  __shared__ float2 bufs[NT * FY::BUF];
-  extern __shared__ __align__(16) float2 A[];   // [N2][LY + 1]
+  __shared__ C tw[TWN];
+  __shared__ C bufs[NT * FY::BUF];
+  extern __shared__ __align__(16) unsigned char sm_dyn[];
+  C *A = reinterpret_cast<C *>(sm_dyn);   // [N2][LY + 1]
   const int rx = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   if (act && !act[b]) return;
   for (int i = threadIdx.x; i < TWN; i += blockDim.x) tw[i] = twg[i];
   __syncthreads();
   const int N1 = g.N[1], N2 = g.N[2], PY = LY + 1;
-  float2 *Tp = T + b * g.Tsz + ((long long)rx * 3 + c) * N2 * N1;   // [m_z][m_y] block
+  C *Tp = T + b * g.Tsz + ((long long)rx * 3 + c) * N2 * N1;   // [m_z][m_y] block
   // y forward: team per m_z row, straight from global memory
   {
     const Lanes ln(FY::TS);
-    float2 w[8];
+    C w[8];
     FY::twiddles(w, ln.lane, tw);
     for (int r0 = 0; r0 < N2; r0 += NTY) {
       const int mz = r0 + ln.team;
       const bool valid = mz < N2;
-      float2 v[8];
+      C v[8];
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int h = harm_at(ln.lane + FY::TS * a, g.n[1], LY);
-        v[a] = (valid && h >= 0) ? Tp[mz * N1 + h] : make_float2(0.f, 0.f);
+        v[a] = (valid && h >= 0) ? Tp[mz * N1 + h] : mk((R)0, (R)0);
       }
       FY::template forward<+1>(v, ln.lane, w, bufs + ln.team * FY::BUF, ln.mask);
       if (valid)
@@ -125,25 +128,25 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, float2 *__restrict__ T, con
   // z forward, times D, z inverse: team per y-frequency column
   {
     const Lanes ln(FZ::TS);
-    float2 w[8];
+    C w[8];
     FZ::twiddles(w, ln.lane, tw);
-    const float *Dx = D + (long long)rx * LY * LZ;
+    const R *Dx = D + (long long)rx * LY * LZ;
     for (int c0 = 0; c0 < LY; c0 += NTZ) {
       const int ry = c0 + ln.team;
       const bool valid = ry < LY;
-      float2 v[8];
+      C v[8];
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int h = harm_at(ln.lane + FZ::TS * a, g.n[2], LZ);
-        v[a] = (valid && h >= 0) ? A[h * PY + ry] : make_float2(0.f, 0.f);
+        v[a] = (valid && h >= 0) ? A[h * PY + ry] : mk((R)0, (R)0);
       }
-      float2 *bf = bufs + ln.team * FZ::BUF;
+      C *bf = bufs + ln.team * FZ::BUF;
       FZ::template forward<+1>(v, ln.lane, w, bf, ln.mask);
       if (valid) {
-        const float *Dc = Dx + (long long)ry * LZ;
+        const R *Dc = Dx + (long long)ry * LZ;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float d = Dc[FZ::freq(ln.lane, q)];
+          const R d = Dc[FZ::freq(ln.lane, q)];
           v[q].x *= d;
           v[q].y *= d;
         }
@@ -161,14 +164,14 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, float2 *__restrict__ T, con
   // y inverse: team per row, straight to global memory
   {
     const Lanes ln(FY::TS);
-    float2 w[8];
+    C w[8];
     FY::twiddles(w, ln.lane, tw);
     for (int r0 = 0; r0 < N2; r0 += NTY) {
       const int mz = r0 + ln.team;
       const bool valid = mz < N2;
-      float2 v[8];
+      C v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = valid ? A[mz * PY + FY::freq(ln.lane, q)] : make_float2(0.f, 0.f);
+      for (int q = 0; q < 8; ++q) v[q] = valid ? A[mz * PY + FY::freq(ln.lane, q)] : mk((R)0, (R)0);
       FY::template inverse<-1>(v, ln.lane, w, bufs + ln.team * FY::BUF, ln.mask);
       if (valid)
 #pragma unroll
@@ -181,24 +184,27 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, float2 *__restrict__ T, con
 }
 
 // MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u)
-template <int L0, int MODE>
-__global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const float2 *__restrict__ T, const float2 *__restrict__ X,
-                                                 long long xstride, float2 *__restrict__ Y, long long ystride,
+template <typename R, int L0, int MODE>
+__global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T *__restrict__ T,
+                                                 const typename Cx<R>::T *__restrict__ X, long long xstride,
+                                                 typename Cx<R>::T *__restrict__ Y, long long ystride,
                                                  const int *__restrict__ act, const Inst *__restrict__ inst,
-                                                 const float *__restrict__ iden, const float2 *__restrict__ twg,
+                                                 const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,
                                                  int rows, double *partial, unsigned *counter, double *norm_out) {
+  using C = typename Cx<R>::T;
   using F = Team8<L0>;
   constexpr int TS = F::TS, NTM = TT / TS;
-  __shared__ float2 tw[TWN];
-  __shared__ float2 bufs[NTM * F::BUF];
+  __shared__ C tw[TWN];
+  __shared__ C bufs[NTM * F::BUF];
   __shared__ double red[32];
-  extern __shared__ __align__(16) float2 S3[];   // [3][rows][N0 + 1], then kx[N0]
+  extern __shared__ __align__(16) unsigned char sm_dyn[];
+  C *S3 = reinterpret_cast<C *>(sm_dyn);   // [3][rows][N0 + 1], then kx[N0]
   const int b = blockIdx.y;
   if (act && !act[b]) return;
   for (int i = threadIdx.x; i < TWN; i += blockDim.x) tw[i] = twg[i];
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2], P = N0 + 1;
-  float *kxs = reinterpret_cast<float *>(S3 + 3 * rows * P);
-  for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (float)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
+  R *kxs = reinterpret_cast<R *>(S3 + 3 * rows * P);
+  for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (R)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
   __syncthreads();
   const long long Nh = g.Nh;
   const long long r0 = (long long)blockIdx.x * rows;
@@ -206,16 +212,16 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const float2 *__restrict
   const int nr = (int)(left < rows ? left : rows);
   {
     const Lanes ln(TS);
-    float2 w[8];
+    C w[8];
     F::twiddles(w, ln.lane, tw);
     const int c = ln.team / rows, row = ln.team - c * rows;
     const bool valid = c < 3 && row < nr;
-    const float2 *Tr = T + b * g.Tsz + r0 + row;
-    float2 v[8];
+    const C *Tr = T + b * g.Tsz + r0 + row;
+    C v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int rx = F::freq(ln.lane, q);
-      v[q] = valid ? Tr[((long long)rx * 3 + c) * N2 * N1] : make_float2(0.f, 0.f);
+      v[q] = valid ? Tr[((long long)rx * 3 + c) * N2 * N1] : mk((R)0, (R)0);
     }
     F::template inverse<-1>(v, ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
     if (valid)
@@ -226,24 +232,24 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const float2 *__restrict
       }
   }
   __syncthreads();
-  const float kb2 = (float)inst[b].kb2;
+  const R kb2 = (R)inst[b].kb2;
   const long long h0 = ((long long)g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
-  const float2 *Xb = X + b * xstride;
-  float2 *Yb = Y + b * ystride;
+  const C *Xb = X + b * xstride;
+  C *Yb = Y + b * ystride;
   double acc = 0;
   for (int e = threadIdx.x; e < nr * N0; e += blockDim.x) {
     const int row = e / N0, mx = e - row * N0;
     const long long rr = r0 + row;
     const int mz = (int)(rr / N1), my = (int)(rr - (long long)mz * N1);
     const long long h = rr * N0 + mx;
-    const float2 u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
+    const C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
                  u2 = S3[(2 * rows + row) * P + mx];
-    const float kx = kxs[mx];
-    const float ky = (float)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
-    const float kz = (float)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
-    const float id = iden[b * Nh + h];
-    const float kux = kx * u0.x + ky * u1.x + kz * u2.x, kuy = kx * u0.y + ky * u1.y + kz * u2.y;
-    float2 y0 = Xb[h], y1 = Xb[Nh + h], y2 = Xb[2 * Nh + h];
+    const R kx = kxs[mx];
+    const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
+    const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
+    const R id = iden[b * Nh + h];
+    const R kux = kx * u0.x + ky * u1.x + kz * u2.x, kuy = kx * u0.y + ky * u1.y + kz * u2.y;
+    C y0 = Xb[h], y1 = Xb[Nh + h], y2 = Xb[2 * Nh + h];
     y0.x -= id * (kb2 * u0.x - kx * kux);
     y0.y -= id * (kb2 * u0.y - kx * kuy);
     y1.x -= id * (kb2 * u1.x - ky * kux);
@@ -251,15 +257,15 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const float2 *__restrict
     y2.x -= id * (kb2 * u2.x - kz * kux);
     y2.y -= id * (kb2 * u2.y - kz * kuy);
     if (MODE == 1) {
-      float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0;
+      C a0 = mk((R)0, (R)0), a1 = a0, a2 = a0;
       if (h == h0) {
-        a0 = make_float2((float)inst[b].a[0], (float)inst[b].a[1]);
-        a1 = make_float2((float)inst[b].a[2], (float)inst[b].a[3]);
-        a2 = make_float2((float)inst[b].a[4], (float)inst[b].a[5]);
+        a0 = mk((R)inst[b].a[0], (R)inst[b].a[1]);
+        a1 = mk((R)inst[b].a[2], (R)inst[b].a[3]);
+        a2 = mk((R)inst[b].a[4], (R)inst[b].a[5]);
       }
-      y0 = make_float2(a0.x - y0.x, a0.y - y0.y);
-      y1 = make_float2(a1.x - y1.x, a1.y - y1.y);
-      y2 = make_float2(a2.x - y2.x, a2.y - y2.y);
+      y0 = mk(a0.x - y0.x, a0.y - y0.y);
+      y1 = mk(a1.x - y1.x, a1.y - y1.y);
+      y2 = mk(a2.x - y2.x, a2.y - y2.y);
     }
     if (norm_out)
       acc += (double)y0.x * y0.x + (double)y0.y * y0.y + (double)y1.x * y1.x + (double)y1.y * y1.y +
@@ -284,55 +290,60 @@ int matvec_reg_blocks_pass3(const Geo &g) {
   return (int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows);
 }
 
-cudaError_t launch_matvec_reg(const MatvecArgs<float> &a, cudaStream_t st, Profiler *prof) {
+template <typename R>
+cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof) {
+  using C = typename Cx<R>::T;
   const Geo &g = a.g;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
+  const double cs = sizeof(C);
   // pass 1
   {
     const int RB = TT / (g.L[0] / 8);
     dim3 grid((int)((3LL * N2 * N1 + RB - 1) / RB), a.B);
     if (prof) prof->begin(KIND_FWD_X, st);
     if (g.L[0] == 64)
-      k_fwd_x_t8<64><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw);
+      k_fwd_x_t8<R, 64><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw);
     else
-      k_fwd_x_t8<32><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw);
-    if (prof) prof->end(KIND_FWD_X, st, (double)a.B * 8.0 * (double)(g.U + g.Tsz));
+      k_fwd_x_t8<R, 32><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw);
+    if (prof) prof->end(KIND_FWD_X, st, (double)a.B * cs * (double)(g.U + g.Tsz));
   }
   // pass 2
   {
-    const size_t smem = sizeof(float2) * (size_t)N2 * (g.L[1] + 1);
+    const size_t smem = sizeof(C) * (size_t)N2 * (g.L[1] + 1);
     dim3 grid(g.L[0], 3, a.B);
     if (prof) prof->begin(KIND_YZ, st);
 #define GSM_YZ(LY, LZ)                                                                                      \
-  cudaFuncSetAttribute(k_yz_t8<LY, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
-  k_yz_t8<LY, LZ><<<grid, TT, smem, st>>>(g, a.T, a.D, a.act, a.tw)
+  cudaFuncSetAttribute(k_yz_t8<R, LY, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+  k_yz_t8<R, LY, LZ><<<grid, TT, smem, st>>>(g, a.T, a.D, a.act, a.tw)
     if (g.L[1] == 64 && g.L[2] == 64) { GSM_YZ(64, 64); }
     else if (g.L[1] == 64) { GSM_YZ(64, 32); }
     else if (g.L[2] == 64) { GSM_YZ(32, 64); }
     else { GSM_YZ(32, 32); }
 #undef GSM_YZ
-    if (prof) prof->end(KIND_YZ, st, (double)a.B * 16.0 * (double)g.Tsz + 4.0 * (double)g.L[0] * g.L[1] * g.L[2]);
+    if (prof) prof->end(KIND_YZ, st, (double)a.B * 2.0 * cs * (double)g.Tsz + sizeof(R) * (double)g.L[0] * g.L[1] * g.L[2]);
   }
   // pass 3
   {
     const int rows = p3_rows(g);
-    const size_t smem = sizeof(float2) * 3 * (size_t)rows * (N0 + 1) + sizeof(float) * N0 + 16;
+    const size_t smem = sizeof(C) * 3 * (size_t)rows * (N0 + 1) + sizeof(R) * N0 + 16;
     dim3 grid((int)(((long long)N1 * N2 + rows - 1) / rows), a.B);
     if (prof) prof->begin(KIND_INV_X, st);
 #define GSM_P3(L0, M)                                                                                          \
-  cudaFuncSetAttribute(k_inv_x_t8<L0, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
-  k_inv_x_t8<L0, M><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden,    \
-                                            a.tw, rows, a.partial, a.counter, a.norm_out)
+  cudaFuncSetAttribute(k_inv_x_t8<R, L0, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+  k_inv_x_t8<R, L0, M><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, \
+                                               a.tw, rows, a.partial, a.counter, a.norm_out)
     if (g.L[0] == 64) {
       if (a.mode == 1) { GSM_P3(64, 1); } else { GSM_P3(64, 0); }
     } else {
       if (a.mode == 1) { GSM_P3(32, 1); } else { GSM_P3(32, 0); }
     }
 #undef GSM_P3
-    if (prof) prof->end(KIND_INV_X, st, (double)a.B * (8.0 * (double)(g.Tsz + 2 * g.U) + 4.0 * (double)g.Nh));
+    if (prof) prof->end(KIND_INV_X, st, (double)a.B * (cs * (double)(g.Tsz + 2 * g.U) + sizeof(R) * (double)g.Nh));
   }
-  (void)N0;
   return cudaGetLastError();
 }
+
+template cudaError_t launch_matvec_reg<float>(const MatvecArgs<float> &, cudaStream_t, Profiler *);
+template cudaError_t launch_matvec_reg<double>(const MatvecArgs<double> &, cudaStream_t, Profiler *);
 
 }  // namespace gsm
