@@ -179,9 +179,10 @@ gsm_status gsm_retrieve_tensor_grad(gsm_plan_t *plan, double k0, const double ka
 /* Per-kernel timing with CUDA events on the plan's stream.  enable = 1 starts
  * recording (and clears totals); gsm_profile_get returns launches, summed
  * device milliseconds and algorithmic bytes for kernel class `kind`
- * (0 x-forward, 1 yz-convolution, 2 x-inverse+Green, 3 Krylov dots,
- * 4 Krylov update, 5 other; 6 = number of kernels the plan launched since
- * gsm_profile, counted whether or not recording is on). */
+ * (0 x-forward, 1 yz-convolution, 2 x-inverse+Green (these three: the
+ * working-precision product), 3 Krylov dots, 4 Krylov update, 5 other,
+ * 6 FP64 residual product (all three passes); 7 = number of kernels the
+ * plan launched since gsm_profile, counted whether or not recording is on). */
 gsm_status gsm_profile(gsm_plan_t *plan, int enable);
 gsm_status gsm_profile_get(gsm_plan_t *plan, int kind, long long *launches,
                            double *total_ms, double *bytes);

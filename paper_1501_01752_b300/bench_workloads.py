@@ -1,0 +1,164 @@
+"""Secondary measurements beside the headline bench (bench.py --workload ...):
+
+sweep     batched resonance sweep for the tensor retrieval: ellipsoid lattice
+          (eps 6, semi-axes 0.4/0.3/0.2 Lambda), 16 frequencies
+          Lambda/lambda = 0.10..0.40 x 16 kappa x 2 polarisations = 512 solves,
+          truncation 15/21/31 harmonics per axis by frequency group, one
+          gsm_sweep call, then the pole fits.
+gyroid    one large near-resonance solve: gyroid g > 0.5 voxels (128^3,
+          eps 12), Lambda = 0.4, 63^3 harmonics (750k unknowns), 128^3 grid,
+          Krylov basis capped to 256 MB; complex64 + refinement and FP64.
+adjoint   gradient of eps_xx - eps_yy with respect to 64^3 voxel
+          permittivities (seeded mirror-symmetric random binary field,
+          eps in {1, 6}, fill 0.3), 21^3 harmonics.
+optimise  50 projected gradient steps on that objective.
+
+Each prints one JSON line.  All inputs are synthetic (workloads.py).
+"""
+from __future__ import annotations
+
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import gsm
+from . import workloads as wl
+
+
+def _mg(eps_i, eps_h, f):
+    b = (eps_i - eps_h) / (eps_i + 2 * eps_h)
+    return eps_h * (1 + 2 * f * b) / (1 - f * b)
+
+
+def _window(k0, n, lo=0.85, hi=1.15):
+    # stay clear of the basis light cone kappa = k0 (eps_b = 1)
+    return max(n * lo, 1.03) * k0, n * hi * k0
+
+
+def run(name, args):
+    torch.cuda.init()
+    {"sweep": sweep, "gyroid": gyroid, "adjoint": adjoint, "optimise": optimise}[name](args)
+
+
+def _events():
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    return a, b
+
+
+def sweep(args):
+    st = wl.ellipsoid_lattice(period=1.0)
+    f = 4 * math.pi / 3 * 0.4 * 0.3 * 0.2
+    n_mg = math.sqrt(_mg(6.0, 1.0, f))
+    plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=64)
+    pts, groups = [], []
+    for gi in range(16):
+        ratio = 0.10 + 0.02 * gi
+        k0 = 2 * math.pi * ratio                 # Lambda = 1
+        N = (15, 21, 31)[gi % 3]
+        lo, hi = _window(k0, n_mg)
+        kap = np.linspace(lo, hi, 16)
+        for pol in ((1, 0, 0), (0, 1, 0)):
+            idx = []
+            for kv in kap:
+                p = wl.point(kv, (0, 0, 1), pol, k0)
+                p["n_harm"] = (N, N, N)
+                idx.append(len(pts))
+                pts.append(p)
+            groups.append((ratio, pol, kap, idx, k0))
+    plan.sweep(pts[:64])                          # warm-up (plan levels, workspaces)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E0, infos = plan.sweep(pts)
+    t_sweep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out = []
+    for ratio, pol, kap, idx, k0 in groups:
+        xi = np.array([np.vdot(np.asarray(pol, complex), E0[i]) for i in idx])
+        eta, zeta = gsm.fit_poles(kap, xi, 5, 10)
+        inside = [j for j in range(5) if kap[0] <= eta[j].real <= kap[-1]]
+        j = max(inside, key=lambda j: abs(zeta[j])) if inside else None
+        out.append(None if j is None else float(((eta[j] / k0) ** 2).real))
+    t_fit = time.perf_counter() - t0
+    iters = [i["iters"] for i in infos]
+    print(json.dumps({
+        "workload": "sweep: ellipsoid lattice eps 6, 16 omega x 16 kappa x 2 pol, N = 15/21/31",
+        "solves": len(pts), "seconds": t_sweep, "solves_per_s": len(pts) / t_sweep,
+        "retrieval_host_ms": 1000 * t_fit, "iters_mean": float(np.mean(iters)),
+        "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
+        "eps_xx_by_ratio": out[0::2], "eps_yy_by_ratio": out[1::2], "n_MG": n_mg}), flush=True)
+    plan.close()
+
+
+def gyroid(args):
+    vox = wl.gyroid_voxels(128, 0.5, (1.0, 12.0))
+    st = dict(periods=(0.4, 0.4, 0.4), voxels=vox)
+    k0 = 2 * math.pi
+    f = float(np.mean(vox > 2))
+    n0 = math.sqrt(_mg(12.0, 1.0, f))
+    # locate the x-polarised mode pole on a 15^3 truncation, then solve at 63^3
+    # just above it (slow Krylov convergence near the resonance)
+    coarse = gsm.plan_for(st, (15, 15, 15), precision=gsm.FP64, tol=1e-10)
+    lo, hi = _window(k0, n0, 0.8, 1.3)
+    eps, diag = coarse.retrieve_tensor(k0, [(lo, hi)] * 3, 16)
+    eta = float(diag["eta"][0].real)
+    coarse.close()
+    pt = wl.point(eta * (1 + 1e-3), (0, 0, 1), (1, 0, 0), k0)
+    res = {"workload": "gyroid g > 0.5 eps 12, Lambda 0.4, 63^3 harmonics, 128^3 grid, 256 MB Krylov cap",
+           "fill": f, "kappa_over_k0": pt["kappa"] / k0, "eta15_over_k0": eta / k0}
+    U = 3 * 63 ** 3
+    for name, prec in (("c64_refine", gsm.FP32_REFINE), ("fp64", gsm.FP64)):
+        plan = gsm.plan_for(st, (63, 63, 63), precision=prec, tol=1e-8, max_batch=1, hbm_cap=256 << 20,
+                            max_iter=20000)
+        E = torch.empty(U, dtype=torch.complex128, device="cuda")
+        a, b = _events()
+        a.record()
+        _, infos, s = plan.solve([pt], out=E)
+        b.record()
+        b.synchronize()
+        res[name] = dict(seconds=a.elapsed_time(b) / 1000, iters=infos[0]["iters"],
+                         refine_steps=infos[0]["refine_steps"], rel_residual=infos[0]["rel_residual"],
+                         status=infos[0]["status"])
+        plan.close()
+    print(json.dumps(res), flush=True)
+
+
+def _c4():
+    vox = wl.random_binary_voxels(64, 1501, 2.0, 0.3, (1.0, 6.0), mirror=True)
+    st = dict(periods=(0.3, 0.3, 0.3), voxels=vox)
+    k0 = 2 * math.pi
+    n0 = math.sqrt(_mg(6.0, 1.0, 0.3))
+    lo, hi = _window(k0, n0)
+    return vox, st, k0, [(lo, hi)] * 3
+
+
+def adjoint(args):
+    vox, st, k0, win = _c4()
+    plan = gsm.plan_for(st, (21, 21, 21), precision=gsm.FP32_REFINE, tol=1e-10, max_batch=64)
+    plan.retrieve_tensor(k0, win, 16)
+    a, b = _events()
+    a.record()
+    eps, grad = plan.retrieve_tensor_grad(k0, win, (1.0, -1.0, 0.0), 16)
+    b.record()
+    b.synchronize()
+    print(json.dumps({"workload": "adjoint: 64^3 mirror-symmetric random voxels, 21^3 harmonics",
+                      "seconds_per_gradient": a.elapsed_time(b) / 1000, "eps": list(map(float, eps)),
+                      "grad_abs_max": float(np.abs(grad).max()), "grad_sum": float(grad.sum())}), flush=True)
+    plan.close()
+
+
+def optimise(args):
+    from .autograd import optimise_anisotropy
+    vox, st, k0, win = _c4()
+    plan = gsm.plan_for(st, (21, 21, 21), precision=gsm.FP32_REFINE, tol=1e-10, max_batch=64)
+    t0 = time.perf_counter()
+    v, hist = optimise_anisotropy(plan, vox, k0, win, steps=max(1, args.steps))
+    dt = time.perf_counter() - t0
+    print(json.dumps({"workload": "optimise eps_xx - eps_yy, 64^3 voxels, 21^3 harmonics",
+                      "steps": len(hist), "seconds": dt, "objective_first": float(hist[0][0] - hist[0][1]),
+                      "objective_last": float(hist[-1][0] - hist[-1][1]), "eps_last": list(map(float, hist[-1]))}),
+          flush=True)
+    plan.close()

@@ -192,7 +192,8 @@ static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nbl
   w.iden32 = (float *)take((size_t)B * g.Nh * 4);
   w.inst = (Inst *)take((size_t)B * sizeof(Inst));
   w.need = (int *)take((size_t)B * 4);
-  const int mvb = std::max(std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8)), matvec_reg_blocks_pass3(g));
+  const int mvb = std::max(std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8)),
+                           std::max(matvec_reg_blocks_pass3(g), krylov_blocks(g, 1)));
   w.mv_partial = (double *)take((size_t)B * mvb * 8);
   w.mv_norm = (double *)take((size_t)B * 8);
   w.mv_counter = (unsigned *)take((size_t)B * 4);
@@ -377,7 +378,8 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   if (const char *ro = std::getenv("GSM_REORTH")) k.force_reorth = std::atoi(ro);
   // pinned staging: instance parameters and the small per-cycle arrays
   auto al = [](size_t n) { return (n + 63) & ~(size_t)63; };
-  const size_t stage = al(B * sizeof(Inst)) + al(B * 4) + al(B * 8) + al(B * 4) + al(B * 8) + al(B * 16) + al(B * 8);
+  const size_t stage =
+      al(B * sizeof(Inst)) + al(B * 4) + al(B * 8) + al(B * 4) + al(B * 8) + al(B * 16) + al(B * 8) + al(B * 4);
   if ((s = ensure_pinned(p, stage))) return s;
   char *sp = p->pin;
   auto grab = [&](size_t n) { char *r = sp; sp += al(n); return (void *)r; };
@@ -388,6 +390,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   double *h_s64 = (double *)grab(B * 8);
   double2 *h_g0 = (double2 *)grab(B * 16);
   double *h_rn = (double *)grab(B * 8);
+  int *h_kc = (int *)grab(B * 4);
   for (int b = 0; b < B; ++b) {
     if ((s = make_inst(p, pts[b], g, hI[b]))) return s;
     if (rhs)
@@ -403,7 +406,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   const double tol = tol_of(p->d), itol = inner_tol_of(p->d);
   const int max_it = max_iter_of(p->d);
   std::vector<double> bnorm(B), rnorm(B);
-  std::vector<int> need(B, 1), iters(B, 0), steps(B, 0), status(B, GSM_OK);
+  std::vector<int> need(B, 1), iters(B, 0), steps(B, 0), status(B, GSM_OK), cert_ok(B, 0);
   for (int b = 0; b < B; ++b) {
     double s2 = 0;
     for (int i = 0; i < 6; ++i) s2 += hI[b].a[i] * hI[b].a[i];
@@ -476,37 +479,63 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       }
       else CK(cudaMemcpyAsync((double2 *)(V + b * vinst), w->r64 + (size_t)b * g.U, g.U * 16, cudaMemcpyDeviceToDevice, st));
     }
-    std::vector<int> act(need);
+    // Arnoldi steps; the host looks at the convergence flags every CHECK
+    // steps (converged instances are masked on the device meanwhile)
+    constexpr int CHECK = 4;
     for (int j = 0; j < m; ++j) {
-      bool live = false;
-      for (int b = 0; b < B; ++b) live |= act[b] != 0;
-      if (!live) break;
       mv.X = V + (long long)j * Us;
       mv.Y = V + (long long)(j + 1) * Us;
       CK(matvec<R>(p, lv, mv, prof));
       CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
       CK(launch_finish(k, j, st));
       p->launches += 3 + (k.force_reorth == 2 ? 2 : 4) + 1;
-      for (int b = 0; b < B; ++b)
-        if (act[b]) iters[b]++;
-      CK(cudaMemcpyAsync(h_act, k.act, B * 4, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int b = 0; b < B; ++b) act[b] = h_act[b];
+      if ((j + 1) % CHECK == 0 && j + 1 < m) {
+        CK(cudaMemcpyAsync(h_act, k.act, B * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        bool live = false;
+        for (int b = 0; b < B; ++b) live |= h_act[b] != 0;
+        if (!live) break;
+      }
     }
     CK(launch_backsolve(k, st));
-    CK(launch_sol_update<R>(k, w->x64, g.U, V, vinst, w->need, st, prof));
-    p->launches += 2 + 3;  // + the FP64 residual below
-    // FP64 residual of the updated iterate
-    if (prof) prof->begin(KIND_OTHER, st);
-    CK(matvec<double>(p, lv, rs, nullptr));
-    if (prof) prof->end(KIND_OTHER, st, 0.0);
+    // complex64 solves keep the correction d in the last basis slot when the
+    // residual will be updated as r -= A d (see below)
+    bool recursive = prec && outer > 0;
+    for (int b = 0; b < B; ++b)
+      if (need[b] && !cert_ok[b]) recursive = false;
+    CK(launch_sol_update<R>(k, w->x64, g.U, V, vinst, w->need, recursive ? m : -1, st, prof));
+    CK(cudaMemcpyAsync(h_kc, k.kcount, B * 4, cudaMemcpyDeviceToHost, st));
+    p->launches += 2;
+    if (!recursive) {
+      // FP64 residual of the updated iterate
+      if (prof) prof->begin(KIND_RESID64, st);
+      CK(matvec<double>(p, lv, rs, nullptr));
+      if (prof) prof->end(KIND_RESID64, st, 16.0 * B * (double)(2 * g.U + 2 * g.Tsz) + 8.0 * (double)g.L[0] * g.L[1] * g.L[2]);
+      p->launches += 3;
+    } else {
+      // r -= A d: A d in complex64 has error ~ eps_mv ||A d|| ~ eps_mv ||r_prev||,
+      // far below tol ||b|| once a certified ||r|| <= 1e-3 ||b|| (cert_ok)
+      MatvecArgs<R> md = mv;
+      md.X = V + (long long)m * Us;
+      md.Y = V;
+      md.scale = nullptr;
+      md.write_back = 0;
+      md.mode = 0;
+      md.act = w->need;
+      CK(matvec<R>(p, lv, md, prof));
+      CK(launch_resid_sub(w->r64, g.U, (const float2 *)V, vinst, g.U, B, k.nblk, w->need, w->mv_partial,
+                          w->mv_counter, w->mv_norm, st));
+      p->launches += 4;
+    }
     CK(cudaMemcpyAsync(h_rn, w->mv_norm, B * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     ++outer;
     for (int b = 0; b < B; ++b) {
       if (!need[b]) continue;
       steps[b]++;
+      iters[b] += h_kc[b];
       rnorm[b] = std::sqrt(std::max(h_rn[b], 0.0));
+      if (!recursive) cert_ok[b] = rnorm[b] <= 1e-3 * bnorm[b];
       if (!std::isfinite(rnorm[b])) {
         need[b] = 0;
         status[b] = GSM_ERR_NOCONV;

@@ -12,7 +12,8 @@ namespace gsm {
 
 constexpr int TWN_HOST = 256;  // twiddle table entries (largest FFT size)
 
-enum ProfKind { KIND_FWD_X = 0, KIND_YZ = 1, KIND_INV_X = 2, KIND_DOTS = 3, KIND_UPDATE = 4, KIND_OTHER = 5, KIND_COUNT = 6 };
+enum ProfKind { KIND_FWD_X = 0, KIND_YZ = 1, KIND_INV_X = 2, KIND_DOTS = 3, KIND_UPDATE = 4, KIND_OTHER = 5,
+                KIND_RESID64 = 6, KIND_COUNT = 7 };
 
 // Records a CUDA event pair around each launch of a kernel class on the
 // launching stream; durations are summed when read.
@@ -136,8 +137,11 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
 cudaError_t launch_finish(const KrylovPtrs &k, int j, cudaStream_t st);
 cudaError_t launch_backsolve(const KrylovPtrs &k, cudaStream_t st);
 template <typename R>
-cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst, const typename Cx<R>::T *V,
-                              long long vinst, const int *need, cudaStream_t st, Profiler *prof);
+cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst, typename Cx<R>::T *V,
+                              long long vinst, const int *need, int dslot, cudaStream_t st, Profiler *prof);
+cudaError_t launch_resid_sub(double2 *r64, long long rinst, const float2 *Ad, long long ainst, long long U, int B,
+                             int nblk, const int *need, double *partial, unsigned *counter, double *norm_out,
+                             cudaStream_t st);
 template <typename C>
 cudaError_t launch_zero_pads(C *V, long long nvec, long long U, long long Us, cudaStream_t st);
 cudaError_t launch_set_rhs(double2 *r64, long long xinst, const Geo &g, const Inst *inst, int B, cudaStream_t st);

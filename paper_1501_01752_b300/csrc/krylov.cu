@@ -313,9 +313,10 @@ __global__ void k_backsolve(KrylovPtrs k) {
 // x += V y (FP64 x; the combination in the basis precision).
 template <typename R>
 __global__ void __launch_bounds__(KT) k_sol_update(double2 *__restrict__ x64, long long xinst,
-                                                   const typename Cx<R>::T *__restrict__ V, long long vinst,
+                                                   typename Cx<R>::T *__restrict__ V, long long vinst,
                                                    long long U, long long Us, const double2 *__restrict__ y, int m,
-                                                   const int *__restrict__ kcount, const int *__restrict__ need) {
+                                                   const int *__restrict__ kcount, const int *__restrict__ need,
+                                                   int dslot) {
   using C = typename Cx<R>::T;
   __shared__ C ys[MAXM];
   const int b = blockIdx.y;
@@ -324,14 +325,46 @@ __global__ void __launch_bounds__(KT) k_sol_update(double2 *__restrict__ x64, lo
   if (n == 0) return;
   for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = mk((R)y[(long long)b * m + i].x, (R)y[(long long)b * m + i].y);
   __syncthreads();
-  const C *Vb = V + b * vinst;
+  C *Vb = V + b * vinst;
   double2 *xb = x64 + b * xinst;
+  C *dv = dslot >= 0 ? Vb + (long long)dslot * Us : nullptr;   // keeps the correction d for r -= A d
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < U; e += (long long)gridDim.x * blockDim.x) {
     C d = mk((R)0, (R)0);
     for (int i = 0; i < n; ++i) d = cadd(d, cmul(ys[i], Vb[(long long)i * Us + e]));
     double2 xv = xb[e];
     xb[e] = mk(xv.x + (double)d.x, xv.y + (double)d.y);
+    if (dv) dv[e] = d;
   }
+}
+
+// r -= A d with A d from the complex64 product, and ||r||^2 (last block).
+__global__ void __launch_bounds__(KT) k_resid_sub(double2 *__restrict__ r64, long long rinst,
+                                                  const float2 *__restrict__ Ad, long long ainst, long long U,
+                                                  const int *__restrict__ need, double *partial, unsigned *counter,
+                                                  double *norm_out) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  if (!need[b]) return;
+  double2 *rb = r64 + b * rinst;
+  const float2 *ab = Ad + b * ainst;
+  double acc = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < U; e += (long long)gridDim.x * blockDim.x) {
+    const float2 a = ab[e];
+    double2 r = rb[e];
+    r.x -= (double)a.x;
+    r.y -= (double)a.y;
+    rb[e] = r;
+    acc += r.x * r.x + r.y * r.y;
+  }
+  last_block_sum(acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
+}
+
+cudaError_t launch_resid_sub(double2 *r64, long long rinst, const float2 *Ad, long long ainst, long long U, int B,
+                             int nblk, const int *need, double *partial, unsigned *counter, double *norm_out,
+                             cudaStream_t st) {
+  dim3 grid(nblk, B);
+  k_resid_sub<<<grid, KT, 0, st>>>(r64, rinst, Ad, ainst, U, need, partial, counter, norm_out);
+  return cudaGetLastError();
 }
 
 // zero the padding (U..Us) of every stored Krylov vector
@@ -411,11 +444,11 @@ cudaError_t launch_backsolve(const KrylovPtrs &k, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst, const typename Cx<R>::T *V,
-                              long long vinst, const int *need, cudaStream_t st, Profiler *prof) {
+cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst, typename Cx<R>::T *V,
+                              long long vinst, const int *need, int dslot, cudaStream_t st, Profiler *prof) {
   dim3 grid(k.nblk, k.B);
   if (prof) prof->begin(KIND_OTHER, st);
-  k_sol_update<R><<<grid, KT, 0, st>>>(x64, xinst, V, vinst, k.U, k.Us, k.y, k.m, k.kcount, need);
+  k_sol_update<R><<<grid, KT, 0, st>>>(x64, xinst, V, vinst, k.U, k.Us, k.y, k.m, k.kcount, need, dslot);
   if (prof) prof->end(KIND_OTHER, st, 0.0);
   return cudaGetLastError();
 }
@@ -435,9 +468,9 @@ cudaError_t launch_extract_e0(const double2 *x64, long long xinst, const Geo &g,
 
 template cudaError_t launch_arnoldi_ortho<float>(const KrylovPtrs &, float2 *, long long, int, cudaStream_t, Profiler *);
 template cudaError_t launch_arnoldi_ortho<double>(const KrylovPtrs &, double2 *, long long, int, cudaStream_t, Profiler *);
-template cudaError_t launch_sol_update<float>(const KrylovPtrs &, double2 *, long long, const float2 *, long long,
-                                              const int *, cudaStream_t, Profiler *);
-template cudaError_t launch_sol_update<double>(const KrylovPtrs &, double2 *, long long, const double2 *, long long,
-                                               const int *, cudaStream_t, Profiler *);
+template cudaError_t launch_sol_update<float>(const KrylovPtrs &, double2 *, long long, float2 *, long long,
+                                              const int *, int, cudaStream_t, Profiler *);
+template cudaError_t launch_sol_update<double>(const KrylovPtrs &, double2 *, long long, double2 *, long long,
+                                               const int *, int, cudaStream_t, Profiler *);
 
 }  // namespace gsm

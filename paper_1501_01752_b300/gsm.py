@@ -22,7 +22,7 @@ STATUS_NAMES = ["GSM_OK", "GSM_ERR_ARG", "GSM_ERR_SINGULAR", "GSM_ERR_NOCONV", "
                 "GSM_ERR_CUDA", "GSM_ERR_TIMEOUT", "GSM_ERR_STATE"]
 FP64, FP32_REFINE = 0, 1
 GMRES, BICGSTAB = 0, 1
-KIND_FWD_X, KIND_YZ, KIND_INV_X, KIND_DOTS, KIND_UPDATE, KIND_OTHER = range(6)
+KIND_FWD_X, KIND_YZ, KIND_INV_X, KIND_DOTS, KIND_UPDATE, KIND_OTHER, KIND_RESID64, KIND_LAUNCHES = range(8)
 
 
 class GsmError(RuntimeError):
