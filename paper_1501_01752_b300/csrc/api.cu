@@ -520,7 +520,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       md.Y = V;
       md.scale = nullptr;
       md.write_back = 0;
-      md.mode = 0;
+      md.mode = adj ? 2 : 0;
       md.act = w->need;
       CK(matvec<R>(p, lv, md, prof));
       CK(launch_resid_sub(w->r64, g.U, (const float2 *)V, vinst, g.U, B, k.nblk, w->need, w->mv_partial,

@@ -238,18 +238,22 @@ class Plan:
         self._check(s, "gsm_apply_noalloc")
         return y
 
-    def solve(self, points, out=None):
-        """Fields for n points: numpy (n, U) complex128 on the host, or into a
-        torch CUDA complex128 tensor `out`.  Returns (E, infos, status)."""
+    def solve(self, points, out=None, host_out=None):
+        """Fields for n points: numpy (n, U) complex128 on the host, into a
+        torch CUDA complex128 tensor `out`, or into a host (e.g. pinned) torch
+        tensor `host_out`.  Returns (E, infos, status)."""
         pts = make_points(points)
         infos = (Info * len(points))()
         total = sum(self.field_size(p) for p in points)
-        if out is None:
-            E = np.zeros(total, dtype=np.complex128)
-            s = lib.gsm_solve(self.h, len(points), pts, ct.c_void_p(E.ctypes.data), 0, infos)
-        else:
+        if out is not None:
             E = out
             s = lib.gsm_solve(self.h, len(points), pts, ct.c_void_p(out.data_ptr()), 1, infos)
+        elif host_out is not None:
+            E = host_out
+            s = lib.gsm_solve(self.h, len(points), pts, ct.c_void_p(host_out.data_ptr()), 0, infos)
+        else:
+            E = np.zeros(total, dtype=np.complex128)
+            s = lib.gsm_solve(self.h, len(points), pts, ct.c_void_p(E.ctypes.data), 0, infos)
         self._check(s, "gsm_solve")
         return E, [dict(iters=i.iters, refine_steps=i.refine_steps, rel_residual=i.rel_residual,
                         status=i.status) for i in infos], s
