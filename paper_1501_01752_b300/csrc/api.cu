@@ -51,7 +51,17 @@ struct Work {
   int *need = nullptr;
   double *mv_partial = nullptr, *mv_norm = nullptr;
   unsigned *mv_counter = nullptr;
+  int *jcount = nullptr;    // device Arnoldi step counter of the captured cycle
   KrylovPtrs k{};
+  struct Cycle { int B, m, adj, force, prec; cudaGraph_t graph; cudaGraphExec_t exec; };
+  std::vector<Cycle> cycles;
+  void drop_graphs() {
+    for (auto &c : cycles) {
+      cudaGraphExecDestroy(c.exec);
+      cudaGraphDestroy(c.graph);
+    }
+    cycles.clear();
+  }
 };
 
 struct Key {
@@ -80,6 +90,8 @@ struct gsm_plan_s {
   Profiler prof;
   long long launches = 0;  // kernels issued by this plan
   bool team_only = false;  // GSM_FFT_PATH=team: shared-memory FFTs everywhere
+  bool use_graphs = true;  // inner GMRES cycles as one graph launch (GSM_GRAPHS=0 disables)
+  cudaStream_t cap_st = nullptr;  // private stream used only to capture graphs
   // pinned host staging
   char *pin = nullptr;
   size_t pin_bytes = 0;
@@ -223,6 +235,8 @@ static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nbl
   k.scale64 = (double *)take((size_t)B * 8);
   k.resid = (double *)take((size_t)B * 8);
   k.force_reorth = 0;
+  k.jdev = nullptr;
+  w.jcount = (int *)take(sizeof(int));
   return off;
 }
 
@@ -239,6 +253,7 @@ static gsm_status get_work(gsm_plan_t *p, const Geo &g, int B, int m, int prec, 
     return GSM_OK;
   }
   if (w.base) {
+    w.drop_graphs();
     cudaFree(w.base);
     w.base = nullptr;
   }
@@ -345,10 +360,71 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
 // for FFT sizes 32/64 (forward and residual forms), the generic
 // shared-memory FFT kernels otherwise.
 template <typename R>
-static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a, Profiler *prof) {
+static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a, Profiler *prof,
+                          cudaStream_t st = nullptr) {
   (void)lv;
-  if (!p->team_only && a.mode < 2 && reg_path_ok(a.g)) return launch_matvec_reg<R>(a, p->st, prof);
-  return launch_matvec<R>(a, p->st, prof);
+  if (!st) st = p->st;
+  if (!p->team_only && a.mode < 2 && reg_path_ok(a.g)) return launch_matvec_reg<R>(a, st, prof);
+  return launch_matvec<R>(a, st, prof);
+}
+
+// One inner GMRES cycle as a graph: a WHILE conditional node whose body is
+// one Arnoldi step (product, Gram-Schmidt, Givens) and k_advance, which
+// moves the device step counter and sets the loop condition.  Built once per
+// workspace, batch size, basis length and operator direction; nullptr if the
+// runtime refuses (the caller then launches step by step).
+template <typename R>
+static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, const MatvecArgs<R> &mv,
+                                   const KrylovPtrs &k, typename Cx<R>::T *V, long long vinst, long long Us, int adj) {
+  const int prec = sizeof(R) == 4;
+  for (auto &c : w->cycles)
+    if (c.B == k.B && c.m == k.m && c.adj == adj && c.force == k.force_reorth && c.prec == prec) return c.exec;
+  if (!p->cap_st && cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  KrylovPtrs kg = k;
+  kg.jdev = w->jcount;
+  MatvecArgs<R> mg = mv;
+  mg.X = V;
+  mg.Y = V + Us;
+  mg.jdev = w->jcount;
+  mg.jstride = Us;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNodeParams np{};
+  cudaGraphNode_t node;
+  ok = ok && cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  if (ok) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(p->cap_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+         cudaSuccess;
+    if (ok) {
+      bool launched = matvec<R>(p, lv, mg, nullptr, p->cap_st) == cudaSuccess &&
+                      launch_arnoldi_ortho<R>(kg, V, vinst, 0, p->cap_st, nullptr) == cudaSuccess &&
+                      launch_finish(kg, 0, p->cap_st) == cudaSuccess &&
+                      launch_advance(kg, h, p->cap_st) == cudaSuccess;
+      cudaGraph_t out = nullptr;
+      ok = cudaStreamEndCapture(p->cap_st, &out) == cudaSuccess && launched;
+    }
+  }
+  ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return nullptr;
+  }
+  w->cycles.push_back({k.B, k.m, adj, k.force_reorth, prec, graph, exec});
+  return exec;
 }
 
 // ------------------------------------------------------------------ solve
@@ -479,22 +555,30 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       }
       else CK(cudaMemcpyAsync((double2 *)(V + b * vinst), w->r64 + (size_t)b * g.U, g.U * 16, cudaMemcpyDeviceToDevice, st));
     }
-    // Arnoldi steps; the host looks at the convergence flags every CHECK
-    // steps (converged instances are masked on the device meanwhile)
-    constexpr int CHECK = 4;
-    for (int j = 0; j < m; ++j) {
-      mv.X = V + (long long)j * Us;
-      mv.Y = V + (long long)(j + 1) * Us;
-      CK(matvec<R>(p, lv, mv, prof));
-      CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
-      CK(launch_finish(k, j, st));
-      p->launches += 3 + (k.force_reorth == 2 ? 2 : 4) + 1;
-      if ((j + 1) % CHECK == 0 && j + 1 < m) {
-        CK(cudaMemcpyAsync(h_act, k.act, B * 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        bool live = false;
-        for (int b = 0; b < B; ++b) live |= h_act[b] != 0;
-        if (!live) break;
+    cudaGraphExec_t cyc = (p->use_graphs && !prof) ? cycle_graph<R>(p, w, lv, mv, k, V, vinst, Us, adj) : nullptr;
+    if (cyc) {
+      // the whole cycle on the device: steps run until every instance has
+      // converged or the basis is full
+      CK(cudaMemsetAsync(w->jcount, 0, sizeof(int), st));
+      CK(cudaGraphLaunch(cyc, st));
+    } else {
+      // Arnoldi steps launched one by one; the host looks at the convergence
+      // flags every CHECK steps (converged instances are masked meanwhile)
+      constexpr int CHECK = 4;
+      for (int j = 0; j < m; ++j) {
+        mv.X = V + (long long)j * Us;
+        mv.Y = V + (long long)(j + 1) * Us;
+        CK(matvec<R>(p, lv, mv, prof));
+        CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
+        CK(launch_finish(k, j, st));
+        p->launches += 3 + (k.force_reorth == 2 ? 2 : 4) + 1;
+        if ((j + 1) % CHECK == 0 && j + 1 < m) {
+          CK(cudaMemcpyAsync(h_act, k.act, B * 4, cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          bool live = false;
+          for (int b = 0; b < B; ++b) live |= h_act[b] != 0;
+          if (!live) break;
+        }
       }
     }
     CK(launch_backsolve(k, st));
@@ -530,6 +614,11 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     CK(cudaMemcpyAsync(h_rn, w->mv_norm, B * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     ++outer;
+    if (cyc) {
+      int steps_run = 0;
+      for (int b = 0; b < B; ++b) steps_run = std::max(steps_run, need[b] ? h_kc[b] : 0);
+      p->launches += (long long)steps_run * (3 + (k.force_reorth == 2 ? 2 : 4) + 2);
+    }
     for (int b = 0; b < B; ++b) {
       if (!need[b]) continue;
       steps[b]++;
@@ -656,6 +745,8 @@ gsm_status gsm_plan(const gsm_plan_desc *desc, gsm_plan_t **out) {
   {
     const char *fp = std::getenv("GSM_FFT_PATH");
     p->team_only = fp && std::strcmp(fp, "team") == 0;
+    const char *gr = std::getenv("GSM_GRAPHS");
+    p->use_graphs = !(gr && std::strcmp(gr, "0") == 0);
   }
   std::vector<double2> t64(TWN_HOST);
   std::vector<float2> t32(TWN_HOST);
@@ -686,7 +777,11 @@ void gsm_plan_destroy(gsm_plan_t *p) {
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
   }
-  for (auto &kv : p->works) cudaFree(kv.second.base);
+  for (auto &kv : p->works) {
+    kv.second.drop_graphs();
+    cudaFree(kv.second.base);
+  }
+  if (p->cap_st) cudaStreamDestroy(p->cap_st);
   cudaFree(p->tw64);
   cudaFree(p->tw32);
   if (p->pin) cudaFreeHost(p->pin);

@@ -87,6 +87,8 @@ template <typename R> struct MatvecArgs {
   double *partial = nullptr;
   unsigned *counter = nullptr;
   double *norm_out = nullptr;  // ||Y||^2 per instance (nullptr = skip)
+  const int *jdev = nullptr;   // graph mode: X and Y advance by (*jdev) * jstride
+  long long jstride = 0;
 };
 
 template <typename R> cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof);
@@ -129,12 +131,15 @@ struct KrylovPtrs {
   double *scale64;          // [B]
   double *resid;            // [B]
   int force_reorth;         // 0: DGKS test, 1: always reorthogonalise, 2: never
+  int *jdev;                // graph mode: Arnoldi step counter on the device (nullptr: host j)
 };
 
 template <typename R>
 cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long long vinst, int j, cudaStream_t st,
                                  Profiler *prof);
 cudaError_t launch_finish(const KrylovPtrs &k, int j, cudaStream_t st);
+// graph mode: j += 1 and set the WHILE condition (any instance active and j < m)
+cudaError_t launch_advance(const KrylovPtrs &k, cudaGraphConditionalHandle h, cudaStream_t st);
 cudaError_t launch_backsolve(const KrylovPtrs &k, cudaStream_t st);
 template <typename R>
 cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst, typename Cx<R>::T *V,

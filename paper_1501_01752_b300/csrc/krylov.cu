@@ -72,7 +72,7 @@ template <typename R>
 __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict__ V, long long vinst, long long Us,
                                              int nv, int wi, const int *__restrict__ act,
                                              const int *__restrict__ gate, double *partial, unsigned *counter,
-                                             double *out, int ostride, int nblk) {
+                                             double *out, int ostride, int nblk, const int *__restrict__ jdev) {
   using C = typename Cx<R>::T;
   constexpr int EPT = Ept<R>::v, NW = KT / 32;
   __shared__ double wsum[2 * GV + 1][NW];
@@ -80,14 +80,18 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
   const int b = blockIdx.y, blk = blockIdx.x % nblk, grp = blockIdx.x / nblk;
   if (!act[b]) return;
   if (gate && !gate[b]) return;
+  if (jdev) {                        // graph mode: the step comes from the device counter
+    nv = *jdev + 1;
+    wi = nv;
+  }
   const int K = 2 * nv + 1, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = grp * GV, i1 = min(nv, i0 + GV), ng = i1 - i0;
+  const int i0 = grp * GV, i1 = min(nv, i0 + GV), ng = max(0, i1 - i0);   // groups past nv only count in
   for (int k = threadIdx.x; k < (2 * GV + 1) * NW; k += blockDim.x) (&wsum[0][0])[k] = 0.0;
   __syncthreads();
   const C *Vb = V + b * vinst;
   const C *W = Vb + (long long)wi * Us;
   const long long ntiles = (Us + KT * EPT - 1) / (KT * EPT);
-  for (long long t = blk; t < ntiles; t += nblk) {
+  for (long long t = blk; ng > 0 && t < ntiles; t += nblk) {
     const long long e0 = t * (KT * EPT) + (long long)threadIdx.x * EPT;
     const bool ok = e0 < Us;
     C w[EPT];
@@ -185,9 +189,13 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
                                                int nv, int wi, const double *__restrict__ h, int hstride,
                                                const int *__restrict__ act, const int *__restrict__ gate,
                                                double *partial, unsigned *counter, double *wn_out,
-                                               int *gate_out, int force) {
+                                               int *gate_out, int force, const int *__restrict__ jdev) {
   using C = typename Cx<R>::T;
   constexpr int EPT = Ept<R>::v;
+  if (jdev) {
+    nv = *jdev + 1;
+    wi = nv;
+  }
   __shared__ C hs[MAXM + 1];
   __shared__ double red[32];
   const int b = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
@@ -241,6 +249,7 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
 // Column j of the Hessenberg matrix, Givens rotations, residual estimate
 // (one thread per instance; Saad's GMRES with complex rotations).
 __global__ void k_finish(KrylovPtrs k, int j) {
+  if (k.jdev) j = *k.jdev;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= k.B || !k.act[b]) return;
   const int m = k.m, hs = 2 * (m + 1) + 1;
@@ -413,28 +422,51 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
                                  Profiler *prof) {
   const int nv = j + 1, wi = j + 1, hs = 2 * (k.m + 1) + 1;
   dim3 grid(k.nblk, k.B);
-  dim3 gdots(k.nblk * ((nv + GV - 1) / GV), k.B);
+  // graph mode sizes the dots grid for the longest basis; blocks past the
+  // current step only take part in the completion count
+  const int ngroups = k.jdev ? (k.m + GV - 1) / GV : (nv + GV - 1) / GV;
+  dim3 gdots(k.nblk * ngroups, k.B);
   const double vb = (double)sizeof(typename Cx<R>::T) * k.U * k.B;  // logical bytes per vector batch
   if (prof) prof->begin(KIND_DOTS, st);
-  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs, k.nblk);
+  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs, k.nblk, k.jdev);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot0, hs, k.act, nullptr, k.partial, k.counter, k.wn0,
-                                   k.gate, k.force_reorth);
+                                   k.gate, k.force_reorth, k.jdev);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   if (k.force_reorth == 2) return cudaGetLastError();   // no second pass: gate was cleared
   if (prof) prof->begin(KIND_DOTS, st);
-  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs, k.nblk);
+  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs, k.nblk, k.jdev);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot1, hs, k.act, k.gate, k.partial, k.counter, k.wn1,
-                                   nullptr, 0);
+                                   nullptr, 0, k.jdev);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   return cudaGetLastError();
 }
 
 cudaError_t launch_finish(const KrylovPtrs &k, int j, cudaStream_t st) {
   k_finish<<<(k.B + 31) / 32, 32, 0, st>>>(k, j);
+  return cudaGetLastError();
+}
+
+// j += 1; the WHILE node goes on while some instance is active and j < m
+__global__ void k_advance(int *jdev, const int *__restrict__ act, int B, int m, cudaGraphConditionalHandle h) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x)
+    if (act[b]) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int j = *jdev + 1;
+    *jdev = j;
+    cudaGraphSetConditional(h, (any && j < m) ? 1u : 0u);
+  }
+}
+
+cudaError_t launch_advance(const KrylovPtrs &k, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_advance<<<1, 256, 0, st>>>(k.jdev, k.act, k.B, k.m, h);
   return cudaGetLastError();
 }
 

@@ -32,11 +32,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
                         typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale, int write_back,
                         const int *__restrict__ act, const Inst *__restrict__ inst,
                         const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg, int rows,
-                        int nchunk) {
+                        int nchunk, const int *__restrict__ jdev, long long jstride) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C *tw = reinterpret_cast<C *>(sm_raw);
   C *S = tw + TWN;
+  if (jdev) X += (long long)(*jdev) * jstride;
   const int b = blockIdx.y;
   if (act && !act[b]) return;
   load_twiddles(tw, twg);
@@ -154,8 +155,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
                         long long xstride, typename Cx<R>::T *__restrict__ Y, long long ystride,
                         const int *__restrict__ act, const Inst *__restrict__ inst, const R *__restrict__ iden,
                         const typename Cx<R>::T *__restrict__ twg, int rows, int nchunk, double *partial,
-                        unsigned *counter, double *norm_out) {
+                        unsigned *counter, double *norm_out, const int *__restrict__ jdev, long long jstride) {
   using C = typename Cx<R>::T;
+  if (jdev) {
+    X += (long long)(*jdev) * jstride;
+    Y += (long long)(*jdev) * jstride;
+  }
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double red[32];
   C *tw = reinterpret_cast<C *>(sm_raw);
@@ -287,11 +292,11 @@ cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *pro
     if (a.mode & 2) {
       cudaFuncSetAttribute(k_fwd_x<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fwd_x<R, true><<<grid, threads, smem, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
-                                                  a.iden, a.tw, rows, nchunk);
+                                                  a.iden, a.tw, rows, nchunk, a.jdev, a.jstride);
     } else {
       cudaFuncSetAttribute(k_fwd_x<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fwd_x<R, false><<<grid, threads, smem, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
-                                                   a.iden, a.tw, rows, nchunk);
+                                                   a.iden, a.tw, rows, nchunk, a.jdev, a.jstride);
     }
     if (prof) prof->end(KIND_FWD_X, st, (double)a.B * (cs * (double)(g.U + g.Tsz)));
   }
@@ -318,7 +323,7 @@ cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *pro
 #define GSM_P3(M)                                                                                               \
   cudaFuncSetAttribute(k_inv_x<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
   k_inv_x<R, M><<<grid, threads, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, a.tw, \
-                                             rows, nchunk, a.partial, a.counter, a.norm_out)
+                                             rows, nchunk, a.partial, a.counter, a.norm_out, a.jdev, a.jstride)
     if (a.mode == 0) { GSM_P3(0); }
     else if (a.mode == 1) { GSM_P3(1); }
     else if (a.mode == 2) { GSM_P3(2); }

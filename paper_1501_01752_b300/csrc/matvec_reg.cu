@@ -43,9 +43,11 @@ template <typename R, int L0>
 __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
                                                  typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
                                                  int write_back, const int *__restrict__ act,
-                                                 const typename Cx<R>::T *__restrict__ twg) {
+                                                 const typename Cx<R>::T *__restrict__ twg, const int *__restrict__ jdev,
+                                                 long long jstride) {
   using C = typename Cx<R>::T;
   using F = Team8<L0>;
+  if (jdev) X += (long long)(*jdev) * jstride;
   constexpr int TS = F::TS, RB = TT / TS;
   __shared__ C tw[TWN];
   __shared__ C bufs[RB * F::BUF];
@@ -190,9 +192,14 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
                                                  typename Cx<R>::T *__restrict__ Y, long long ystride,
                                                  const int *__restrict__ act, const Inst *__restrict__ inst,
                                                  const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,
-                                                 int rows, double *partial, unsigned *counter, double *norm_out) {
+                                                 int rows, double *partial, unsigned *counter, double *norm_out,
+                                                 const int *__restrict__ jdev, long long jstride) {
   using C = typename Cx<R>::T;
   using F = Team8<L0>;
+  if (jdev) {
+    X += (long long)(*jdev) * jstride;
+    Y += (long long)(*jdev) * jstride;
+  }
   constexpr int TS = F::TS, NTM = TT / TS;
   __shared__ C tw[TWN];
   __shared__ C bufs[NTM * F::BUF];
@@ -302,9 +309,11 @@ cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler 
     dim3 grid((int)((3LL * N2 * N1 + RB - 1) / RB), a.B);
     if (prof) prof->begin(KIND_FWD_X, st);
     if (g.L[0] == 64)
-      k_fwd_x_t8<R, 64><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw);
+      k_fwd_x_t8<R, 64><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw, a.jdev,
+                                             a.jstride);
     else
-      k_fwd_x_t8<R, 32><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw);
+      k_fwd_x_t8<R, 32><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw, a.jdev,
+                                             a.jstride);
     if (prof) prof->end(KIND_FWD_X, st, (double)a.B * cs * (double)(g.U + g.Tsz));
   }
   // pass 2
@@ -331,7 +340,7 @@ cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler 
 #define GSM_P3(L0, M)                                                                                          \
   cudaFuncSetAttribute(k_inv_x_t8<R, L0, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
   k_inv_x_t8<R, L0, M><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, \
-                                               a.tw, rows, a.partial, a.counter, a.norm_out)
+                                               a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, a.jstride)
     if (g.L[0] == 64) {
       if (a.mode == 1) { GSM_P3(64, 1); } else { GSM_P3(64, 0); }
     } else {
