@@ -256,12 +256,14 @@ def main():
     h2d = B * 88  # instance parameters (kinc, k_b^2, polarisation) per point
     d2h = B * U * 16
 
-    # plain FP64 GPU path on the same batch
-    p64 = make_plan(gsm.FP64)
-    p64.solve(pts, out=E)
-    t64, infos64 = timed(p64, args.fp64_steps, E)
-    fp64_value = B * args.fp64_steps / t64
-    p64.close()
+    # plain FP64 GPU path on the same batch (--fp64-steps 0 skips it)
+    fp64_value, infos64 = None, None
+    if args.fp64_steps > 0:
+        p64 = make_plan(gsm.FP64)
+        p64.solve(pts, out=E)
+        t64, infos64 = timed(p64, args.fp64_steps, E)
+        fp64_value = B * args.fp64_steps / t64
+        p64.close()
 
     peak, peak_kind = peaks()
     # dominant kernel with a byte count (the "other" bucket is bookkeeping)
@@ -276,8 +278,9 @@ def main():
         "config": {"workload": "woodpile eps 11.9 in eps_b 1, Lambda 0.35, 31^3 harmonics, 64^3 FFT grid",
                    "global_batch": B * ws, "tol": TOL, "l2": "flushed between steps (inputs+basis > L2)",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "fp64_plain": {"value": fp64_value, "unit": "solves/s", "iters_mean": float(np.mean([i["iters"] for i in infos64]))},
-        "speedup_vs_fp64": value / ws / fp64_value,
+        "fp64_plain": None if fp64_value is None else
+        {"value": fp64_value, "unit": "solves/s", "iters_mean": float(np.mean([i["iters"] for i in infos64]))},
+        "speedup_vs_fp64": None if fp64_value is None else value / ws / fp64_value,
         "iters_mean": float(np.mean(iters)), "refine_steps_mean": float(np.mean([i["refine_steps"] for i in infos])),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -288,6 +291,7 @@ def main():
         "profiled_ms_per_step": 1000 * t_prof / args.steps,
         "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        "autotuned_blocks": list(plan.tuned_blocks(gsm.FP32_REFINE)),
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu:

@@ -204,6 +204,13 @@ gsm_status gsm_profile_get(gsm_plan_t *plan, int kind, long long *launches,
  * set; the call synchronises the plan's stream. */
 gsm_status gsm_apply_noalloc(gsm_plan_t *plan, const gsm_point *point, const double *x, double *y);
 
+/* Threads per block that the autotuner chose for the three passes of the
+ * lane-team product (FFT sizes 32/64) of the plan's full truncation in the
+ * given precision: each pass is timed at 128, 256 and 512 threads on the
+ * first batch solved and the fastest is kept (256 before that, or with
+ * GSM_AUTOTUNE=0 in the environment).  GSM_ERR_STATE before the first solve. */
+gsm_status gsm_tuned_blocks(const gsm_plan_t *plan, int precision, int blocks[3]);
+
 const char *gsm_last_error(const gsm_plan_t *plan);
 const char *gsm_version(void);
 

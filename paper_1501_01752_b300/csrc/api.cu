@@ -35,6 +35,8 @@ struct Level {
   Geo g;
   double *D64 = nullptr;
   float *D32 = nullptr;
+  int tb[2][3] = {{256, 256, 256}, {256, 256, 256}};  // lane-team block sizes per pass, [FP64, complex64]
+  bool tuned[2] = {false, false};
 };
 
 // Device workspace for one level, sized for B instances and a basis of m+1.
@@ -364,8 +366,56 @@ static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a
                           cudaStream_t st = nullptr) {
   (void)lv;
   if (!st) st = p->st;
-  if (!p->team_only && a.mode < 2 && reg_path_ok(a.g)) return launch_matvec_reg<R>(a, st, prof);
+  if (!p->team_only && a.mode < 2 && reg_path_ok(a.g))
+    return launch_matvec_reg<R>(a, st, prof, lv.tb[sizeof(R) == 4 ? 1 : 0]);
   return launch_matvec<R>(a, st, prof);
+}
+
+// Autotuner of the lane-team product: for each pass, time the block sizes
+// 128, 256 and 512 threads (one warm-up and three timed launches each, CUDA
+// events on the plan's stream) on the batch about to be solved and keep the
+// fastest.  Runs once per level and precision; GSM_AUTOTUNE=0 keeps 256.
+template <typename R>
+static cudaError_t autotune(gsm_plan_t *p, Level &lv, const MatvecArgs<R> &base) {
+  const int prec = sizeof(R) == 4 ? 1 : 0;
+  if (lv.tuned[prec] || p->team_only || !reg_path_ok(base.g)) return cudaSuccess;
+  lv.tuned[prec] = true;
+  if (const char *at = std::getenv("GSM_AUTOTUNE"))
+    if (std::strcmp(at, "0") == 0) return cudaSuccess;
+  MatvecArgs<R> a = base;
+  a.scale = nullptr;
+  a.write_back = 0;
+  a.act = nullptr;
+  a.norm_out = nullptr;
+  a.mode = 0;
+  a.jdev = nullptr;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cand[3] = {128, 256, 512};
+  for (int pass = 1; pass <= 3; ++pass) {
+    float best = 1e30f;
+    for (int c = 0; c < 3; ++c) {
+      cudaError_t e = launch_reg_pass<R>(pass, cand[c], a, p->st);
+      cudaEventRecord(e0, p->st);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_reg_pass<R>(pass, cand[c], a, p->st);
+      cudaEventRecord(e1, p->st);
+      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        lv.tb[prec][pass - 1] = cand[c];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->launches += 3 * 3 * 4;
+  return cudaGetLastError();
 }
 
 // One inner GMRES cycle as a graph: a WHILE conditional node whose body is
@@ -525,6 +575,14 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   rs.partial = w->mv_partial;
   rs.counter = w->mv_counter;
   rs.norm_out = w->mv_norm;
+  // block sizes of the lane-team kernels: measured on this batch, first use only
+  {
+    MatvecArgs<R> tune = mv;
+    tune.X = V;
+    tune.Y = V + Us;
+    CK(cudaMemsetAsync(V, 0, (size_t)2 * Us * sizeof(C), st));
+    CK(autotune<R>(p, lv, tune));
+  }
   int outer = 0;
   while (true) {
     bool any = false;
@@ -1013,6 +1071,16 @@ extern "C" gsm_status gsm_retrieve_tensor(gsm_plan_t *p, double k0, const double
       diag[4 * c + 3] = zeta[j].imag();
     }
   }
+  return GSM_OK;
+}
+
+extern "C" gsm_status gsm_tuned_blocks(const gsm_plan_t *p, int precision, int blocks[3]) {
+  if (!p || !blocks) return GSM_ERR_ARG;
+  Key key{{p->d.n_harm[0], p->d.n_harm[1], p->d.n_harm[2]}};
+  auto it = p->levels.find(key);
+  if (it == p->levels.end()) return GSM_ERR_STATE;
+  const int prec = precision == GSM_FP32_REFINE ? 1 : 0;
+  for (int i = 0; i < 3; ++i) blocks[i] = it->second.tb[prec][i];
   return GSM_OK;
 }
 

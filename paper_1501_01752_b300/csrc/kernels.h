@@ -94,7 +94,10 @@ template <typename R> struct MatvecArgs {
 template <typename R> cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof);
 // team-of-lanes FFT path for FFT sizes 32/64 on every axis (modes 0, 1)
 bool reg_path_ok(const Geo &g);
-template <typename R> cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof);
+template <typename R>
+cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof, const int *tb);
+// one pass (1, 2, 3) with block size tb in {128, 256, 512} (autotuner)
+template <typename R> cudaError_t launch_reg_pass(int pass, int tb, const MatvecArgs<R> &a, cudaStream_t st);
 int matvec_reg_blocks_pass3(const Geo &g);
 int matvec_blocks_pass3(const Geo &g, size_t csize);
 size_t matvec_max_smem(const Geo &g, size_t csize);

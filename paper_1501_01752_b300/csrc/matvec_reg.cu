@@ -26,7 +26,7 @@ __device__ __forceinline__ int harm_at(int k, int n, int L) {
   return -1;
 }
 
-constexpr int TT = 256;  // threads per block
+constexpr int TB_DEFAULT = 256;  // threads per block unless the autotuner picks another
 
 struct Lanes {
   int team, lane;
@@ -39,7 +39,7 @@ struct Lanes {
   }
 };
 
-template <typename R, int L0>
+template <typename R, int L0, int TT>
 __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
                                                  typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
                                                  int write_back, const int *__restrict__ act,
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__res
   }
 }
 
-template <typename R, int LY, int LZ>
+template <typename R, int LY, int LZ, int TT>
 __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restrict__ T, const R *__restrict__ D,
                                               const int *__restrict__ act, const typename Cx<R>::T *__restrict__ twg) {
   using C = typename Cx<R>::T;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
 }
 
 // MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u)
-template <typename R, int L0, int MODE>
+template <typename R, int L0, int MODE, int TT>
 __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T *__restrict__ T,
                                                  const typename Cx<R>::T *__restrict__ X, long long xstride,
                                                  typename Cx<R>::T *__restrict__ Y, long long ystride,
@@ -289,70 +289,103 @@ bool reg_path_ok(const Geo &g) {
   return ok(g.L[0]) && ok(g.L[1]) && ok(g.L[2]);
 }
 
-static int p3_rows(const Geo &g) { return (TT / (g.L[0] / 8)) / 3; }
+static int p3_rows(const Geo &g, int tb) { return (tb / (g.L[0] / 8)) / 3; }
 
 int matvec_reg_blocks_pass3(const Geo &g) {
   if (!reg_path_ok(g)) return 1;
-  const int rows = p3_rows(g);
+  const int rows = p3_rows(g, 128);   // the smallest block the autotuner may pick
   return (int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows);
 }
 
-template <typename R>
-cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof) {
+template <typename R, int TT>
+static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
+  const Geo &g = a.g;
+  const int RB = TT / (g.L[0] / 8);
+  dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
+  if (g.L[0] == 64)
+    k_fwd_x_t8<R, 64, TT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw, a.jdev,
+                                               a.jstride);
+  else
+    k_fwd_x_t8<R, 32, TT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw, a.jdev,
+                                               a.jstride);
+}
+
+template <typename R, int TT>
+static void pass2(const MatvecArgs<R> &a, cudaStream_t st) {
   using C = typename Cx<R>::T;
   const Geo &g = a.g;
-  const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
-  const double cs = sizeof(C);
-  // pass 1
-  {
-    const int RB = TT / (g.L[0] / 8);
-    dim3 grid((int)((3LL * N2 * N1 + RB - 1) / RB), a.B);
-    if (prof) prof->begin(KIND_FWD_X, st);
-    if (g.L[0] == 64)
-      k_fwd_x_t8<R, 64><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw, a.jdev,
-                                             a.jstride);
-    else
-      k_fwd_x_t8<R, 32><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw, a.jdev,
-                                             a.jstride);
-    if (prof) prof->end(KIND_FWD_X, st, (double)a.B * cs * (double)(g.U + g.Tsz));
-  }
-  // pass 2
-  {
-    const size_t smem = sizeof(C) * (size_t)N2 * (g.L[1] + 1);
-    dim3 grid(g.L[0], 3, a.B);
-    if (prof) prof->begin(KIND_YZ, st);
+  const size_t smem = sizeof(C) * (size_t)g.N[2] * (g.L[1] + 1);
+  dim3 grid(g.L[0], 3, a.B);
 #define GSM_YZ(LY, LZ)                                                                                      \
-  cudaFuncSetAttribute(k_yz_t8<R, LY, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
-  k_yz_t8<R, LY, LZ><<<grid, TT, smem, st>>>(g, a.T, a.D, a.act, a.tw)
-    if (g.L[1] == 64 && g.L[2] == 64) { GSM_YZ(64, 64); }
-    else if (g.L[1] == 64) { GSM_YZ(64, 32); }
-    else if (g.L[2] == 64) { GSM_YZ(32, 64); }
-    else { GSM_YZ(32, 32); }
+  cudaFuncSetAttribute(k_yz_t8<R, LY, LZ, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+  k_yz_t8<R, LY, LZ, TT><<<grid, TT, smem, st>>>(g, a.T, a.D, a.act, a.tw)
+  if (g.L[1] == 64 && g.L[2] == 64) { GSM_YZ(64, 64); }
+  else if (g.L[1] == 64) { GSM_YZ(64, 32); }
+  else if (g.L[2] == 64) { GSM_YZ(32, 64); }
+  else { GSM_YZ(32, 32); }
 #undef GSM_YZ
-    if (prof) prof->end(KIND_YZ, st, (double)a.B * 2.0 * cs * (double)g.Tsz + sizeof(R) * (double)g.L[0] * g.L[1] * g.L[2]);
-  }
-  // pass 3
-  {
-    const int rows = p3_rows(g);
-    const size_t smem = sizeof(C) * 3 * (size_t)rows * (N0 + 1) + sizeof(R) * N0 + 16;
-    dim3 grid((int)(((long long)N1 * N2 + rows - 1) / rows), a.B);
-    if (prof) prof->begin(KIND_INV_X, st);
+}
+
+template <typename R, int TT>
+static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
+  using C = typename Cx<R>::T;
+  const Geo &g = a.g;
+  const int rows = p3_rows(g, TT);
+  const size_t smem = sizeof(C) * 3 * (size_t)rows * (g.N[0] + 1) + sizeof(R) * g.N[0] + 16;
+  dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);
 #define GSM_P3(L0, M)                                                                                          \
-  cudaFuncSetAttribute(k_inv_x_t8<R, L0, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
-  k_inv_x_t8<R, L0, M><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, \
-                                               a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, a.jstride)
-    if (g.L[0] == 64) {
-      if (a.mode == 1) { GSM_P3(64, 1); } else { GSM_P3(64, 0); }
-    } else {
-      if (a.mode == 1) { GSM_P3(32, 1); } else { GSM_P3(32, 0); }
-    }
-#undef GSM_P3
-    if (prof) prof->end(KIND_INV_X, st, (double)a.B * (cs * (double)(g.Tsz + 2 * g.U) + sizeof(R) * (double)g.Nh));
+  cudaFuncSetAttribute(k_inv_x_t8<R, L0, M, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+  k_inv_x_t8<R, L0, M, TT><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, \
+                                                   a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, a.jstride)
+  if (g.L[0] == 64) {
+    if (a.mode == 1) { GSM_P3(64, 1); } else { GSM_P3(64, 0); }
+  } else {
+    if (a.mode == 1) { GSM_P3(32, 1); } else { GSM_P3(32, 0); }
   }
+#undef GSM_P3
+}
+
+template <typename R, template <typename, int> class F>
+static cudaError_t dispatch_tb(int tb, const MatvecArgs<R> &a, cudaStream_t st) {
+  if (tb == 128) F<R, 128>::run(a, st);
+  else if (tb == 512) F<R, 512>::run(a, st);
+  else F<R, 256>::run(a, st);
+  return cudaGetLastError();
+}
+template <typename R, int TT> struct P1 { static void run(const MatvecArgs<R> &a, cudaStream_t st) { pass1<R, TT>(a, st); } };
+template <typename R, int TT> struct P2 { static void run(const MatvecArgs<R> &a, cudaStream_t st) { pass2<R, TT>(a, st); } };
+template <typename R, int TT> struct P3 { static void run(const MatvecArgs<R> &a, cudaStream_t st) { pass3<R, TT>(a, st); } };
+
+// One pass of the lane-team product with a given block size (autotuner).
+template <typename R>
+cudaError_t launch_reg_pass(int pass, int tb, const MatvecArgs<R> &a, cudaStream_t st) {
+  if (pass == 1) return dispatch_tb<R, P1>(tb, a, st);
+  if (pass == 2) return dispatch_tb<R, P2>(tb, a, st);
+  return dispatch_tb<R, P3>(tb, a, st);
+}
+
+template <typename R>
+cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof, const int *tb) {
+  using C = typename Cx<R>::T;
+  const Geo &g = a.g;
+  const double cs = sizeof(C);
+  const int t1 = tb ? tb[0] : TB_DEFAULT, t2 = tb ? tb[1] : TB_DEFAULT, t3 = tb ? tb[2] : TB_DEFAULT;
+  cudaError_t e;
+  if (prof) prof->begin(KIND_FWD_X, st);
+  if ((e = launch_reg_pass<R>(1, t1, a, st)) != cudaSuccess) return e;
+  if (prof) prof->end(KIND_FWD_X, st, (double)a.B * cs * (double)(g.U + g.Tsz));
+  if (prof) prof->begin(KIND_YZ, st);
+  if ((e = launch_reg_pass<R>(2, t2, a, st)) != cudaSuccess) return e;
+  if (prof) prof->end(KIND_YZ, st, (double)a.B * 2.0 * cs * (double)g.Tsz + sizeof(R) * (double)g.L[0] * g.L[1] * g.L[2]);
+  if (prof) prof->begin(KIND_INV_X, st);
+  if ((e = launch_reg_pass<R>(3, t3, a, st)) != cudaSuccess) return e;
+  if (prof) prof->end(KIND_INV_X, st, (double)a.B * (cs * (double)(g.Tsz + 2 * g.U) + sizeof(R) * (double)g.Nh));
   return cudaGetLastError();
 }
 
-template cudaError_t launch_matvec_reg<float>(const MatvecArgs<float> &, cudaStream_t, Profiler *);
-template cudaError_t launch_matvec_reg<double>(const MatvecArgs<double> &, cudaStream_t, Profiler *);
+template cudaError_t launch_matvec_reg<float>(const MatvecArgs<float> &, cudaStream_t, Profiler *, const int *);
+template cudaError_t launch_matvec_reg<double>(const MatvecArgs<double> &, cudaStream_t, Profiler *, const int *);
+template cudaError_t launch_reg_pass<float>(int, int, const MatvecArgs<float> &, cudaStream_t);
+template cudaError_t launch_reg_pass<double>(int, int, const MatvecArgs<double> &, cudaStream_t);
 
 }  // namespace gsm

@@ -74,6 +74,7 @@ def _load():
         "gsm_adjoint": (ct.c_int, [P, ct.c_int, ct.POINTER(Point), dp, dp]),
         "gsm_retrieve_tensor_grad": (ct.c_int, [P, ct.c_double, dp, ct.c_int, ct.c_int, ct.c_int, dp, dp, dp]),
         "gsm_profile": (ct.c_int, [P, ct.c_int]),
+        "gsm_tuned_blocks": (ct.c_int, [P, ct.c_int, ct.POINTER(ct.c_int)]),
         "gsm_profile_get": (ct.c_int, [P, ct.c_int, ct.POINTER(ct.c_longlong), dp, dp]),
         "gsm_last_error": (ct.c_char_p, [P]),
         "gsm_version": (ct.c_char_p, []),
@@ -293,6 +294,12 @@ class Plan:
         s = lib.gsm_retrieve_tensor_grad(self.h, k0, _dp(lohi), n_kappa, Np, Nd, _dp(w), _dp(eps), _dp(out))
         self._check(s, "gsm_retrieve_tensor_grad")
         return eps, out.reshape(self.M)
+
+    def tuned_blocks(self, precision=FP32_REFINE):
+        """Autotuned threads per block of the three product passes."""
+        out = (ct.c_int * 3)()
+        self._check(lib.gsm_tuned_blocks(self.h, precision, out), "gsm_tuned_blocks")
+        return tuple(out)
 
     def profile(self, enable=True):
         self._check(lib.gsm_profile(self.h, int(enable)), "gsm_profile")
