@@ -1,0 +1,70 @@
+"""Full-size configurations through the CUDA path, checked against the oracle
+on what it can compute at these sizes: the oracle's own residual of the GPU
+field (any size), and sampled points solved by the oracle one by one."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import operator as oop
+from oracle import retrieval as ort
+from paper_1501_01752_b300 import workloads as wl
+
+from gpu_common import K0, gsm, oracle_structure, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_residual(st, n_harm, eps_b, pt, E):
+    ost = oracle_structure(st)
+    Delta = ost.delta(n_harm, eps_b)
+    kinc = pt["kappa"] * np.asarray(pt["kdir"])
+    A = oop.Operator(Delta, n_harm, kinc, st["periods"], pt["k0"] ** 2 * eps_b)
+    b = oop.incident(pt["pol"], n_harm)
+    return float(np.linalg.norm(b - A(E.reshape(b.shape))) / np.linalg.norm(b))
+
+
+def test_gyroid_63_near_resonance_under_hbm_cap():
+    # 63^3 harmonics (750k unknowns), 128^3 grid, Krylov basis capped to 64 MB
+    # (restarted GMRES), kappa just above the x-polarised mode pole
+    g = gsm()
+    vox = wl.gyroid_voxels(128, 0.5, (1.0, 12.0))
+    st = dict(periods=(0.4, 0.4, 0.4), voxels=vox)
+    n_harm = (63, 63, 63)
+    pt = wl.point(1.5554 * K0, (0, 0, 1), (1, 0, 0))
+    plan = g.plan_for(st, n_harm, precision=g.FP32_REFINE, tol=1e-8, max_batch=1, hbm_cap=64 << 20,
+                      max_iter=20000)
+    E, infos, s = plan.solve([pt])
+    plan.close()
+    assert s == 0 and infos[0]["rel_residual"] <= 1e-8
+    assert _oracle_residual(st, n_harm, 1.0, pt, E) <= 1.5e-8
+
+
+def test_mixed_truncation_sweep_matches_single_solves_and_oracle():
+    # the ellipsoid sweep of the retrieval: truncations 15/21/31 in one call;
+    # every E_0 equals the one from a separate solve, and sampled points
+    # equal the oracle's
+    g = gsm()
+    st = wl.ellipsoid_lattice(period=1.0)
+    pts = []
+    for gi, N in enumerate((15, 21, 31)):
+        k0 = 2 * math.pi * (0.2 + 0.05 * gi)
+        for kap in (1.08, 1.12):
+            p = wl.point(kap * k0, (0, 0, 1), (1, 0, 0) if gi % 2 else (0, 1, 0), k0)
+            p["n_harm"] = (N, N, N)
+            pts.append(p)
+    plan = g.plan_for(st, (31, 31, 31), precision=g.FP32_REFINE, tol=1e-10, max_batch=64)
+    E0, infos = plan.sweep(pts)
+    for i in (0, 2, 5):
+        Ei, _, _ = plan.solve([pts[i]])
+        N = pts[i]["n_harm"]
+        n = (N[0] - 1) // 2
+        e0 = Ei.reshape((3,) + N[::-1])[:, n, n, n]
+        assert np.max(np.abs(e0 - E0[i])) < 1e-8 * np.max(np.abs(E0[i]))
+    plan.close()
+    ost = oracle_structure(st)
+    for i in (0, 2):
+        p = pts[i]
+        E, _ = ort.solve_point(ost, p["n_harm"], 1.0, p["k0"], p["kdir"], p["kappa"], p["pol"], tol=1e-12)
+        want = ort.zeroth_order(E, p["n_harm"])
+        assert rel(E0[i], want) < 1e-7, (i, rel(E0[i], want))
