@@ -162,7 +162,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="woodpile",
-                    choices=["woodpile", "sweep", "gyroid", "adjoint", "optimise"])
+                    choices=["woodpile", "matvec", "sweep", "gyroid", "adjoint", "optimise"])
     args = ap.parse_args()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":

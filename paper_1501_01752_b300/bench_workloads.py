@@ -1,5 +1,9 @@
 """Secondary measurements beside the headline bench (bench.py --workload ...):
 
+matvec    the Eq. 4 product alone: woodpile 31^3 harmonics, 64^3 grid, 32
+          instances per launch, complex64 and FP64; per-pass device time,
+          algorithmic GB/s and matvecs/s (also the small, clean target for
+          ncu captures of the three product kernels).
 sweep     batched resonance sweep for the tensor retrieval: ellipsoid lattice
           (eps 6, semi-axes 0.4/0.3/0.2 Lambda), 16 frequencies
           Lambda/lambda = 0.10..0.40 x 16 kappa x 2 polarisations = 512 solves,
@@ -40,13 +44,57 @@ def _window(k0, n, lo=0.85, hi=1.15):
 
 def run(name, args):
     torch.cuda.init()
-    {"sweep": sweep, "gyroid": gyroid, "adjoint": adjoint, "optimise": optimise}[name](args)
+    {"matvec": matvec, "sweep": sweep, "gyroid": gyroid, "adjoint": adjoint, "optimise": optimise}[name](args)
 
 
 def _events():
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     return a, b
+
+
+def matvec(args):
+    peak = _hbm_peak()
+    st = wl.woodpile()
+    pts = wl.woodpile_batch(32)
+    B, U = len(pts), 3 * 31 ** 3
+    plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=B)
+    plan.solve(pts[:B])                       # builds the level and runs the block-size autotuner
+    x = wl.random_field((31, 31, 31), 1501, B)
+    xd = torch.from_numpy(x.reshape(B, U)).cuda()
+    res = {"workload": "woodpile 31^3 harmonics, 64^3 grid, %d instances per product" % B,
+           "autotuned_blocks": list(plan.tuned_blocks())}
+    reps = max(3, int(getattr(args, "steps", 10)))
+    for name, prec in (("c64", gsm.FP32_REFINE), ("fp64", gsm.FP64)):
+        for _ in range(3):
+            plan.apply(pts, xd, precision=prec)
+        plan.profile(True)
+        for _ in range(reps):
+            plan.apply(pts, xd, precision=prec)
+        out = {}
+        tot = 0.0
+        for kname, kind in (("fwd_x", gsm.KIND_FWD_X), ("yz_conv", gsm.KIND_YZ), ("inv_x_green", gsm.KIND_INV_X)):
+            n, ms, by = plan.profile_get(kind)
+            tot += ms
+            gbs = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+            out[kname] = {"launches": n, "us_per_launch": 1e3 * ms / max(n, 1), "GB/s": gbs,
+                          "frac_of_measured_hbm": gbs / peak}
+        plan.profile(False)
+        out["matvecs_per_s"] = B * reps / (tot * 1e-3)
+        out["us_per_product_of_%d" % B] = 1e3 * tot / reps
+        res[name] = out
+    plan.close()
+    print(json.dumps(res), flush=True)
+
+
+def _hbm_peak():
+    import os
+    p = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6400.0
 
 
 def sweep(args):

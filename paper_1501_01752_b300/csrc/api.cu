@@ -934,7 +934,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.iden = w->iden32;
     a.tw = p->tw32;
     a.mode = adjoint ? 2 : 0;
-    CK(matvec<float>(p, *lv, a, nullptr));
+    CK(matvec<float>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
     CK(launch_convert_f2d(yf, yd, (long long)n * g.U, st));
   } else {
     MatvecArgs<double> a;
@@ -950,7 +950,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.iden = w->iden64;
     a.tw = p->tw64;
     a.mode = adjoint ? 2 : 0;
-    CK(matvec<double>(p, *lv, a, nullptr));
+    CK(matvec<double>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
   }
   CK(cudaMemcpyAsync(y, yd, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -13,7 +13,7 @@
 //   (TS-point DFTs over s, twiddle, transpose, 8-point DFTs over p).
 // The team buffer holds 8 x 9 complex values (row pitch 9 keeps the
 // transpose free of bank conflicts).  Each lane keeps its own twiddles
-// w_L^{lane k}, k < 8, in registers.
+// w_L^{lane k}, k < 8, in registers, read once from the global table.
 #pragma once
 #include "fft.cuh"
 
@@ -28,10 +28,11 @@ template <int L> struct Team8 {
     return TS == 8 ? lane + 8 * r : (lane + 4 * (r / 4)) + 8 * (r % 4);
   }
 
-  // lane twiddles w_L^{lane k} (k < 8) from the 256-entry table
+  // lane twiddles w_L^{lane k} (k < 8) from the 256-entry table in global
+  // memory (2 or 4 KB: it stays in L1 after the first warps touch it)
   template <typename C> __device__ static __forceinline__ void twiddles(C (&w)[8], int lane, const C *tw) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) w[k] = tw[((lane * k) % L) * (TWN / L)];
+    for (int k = 0; k < 8; ++k) w[k] = __ldg(&tw[((lane * k) % L) * (TWN / L)]);
   }
 
   template <int S, typename C> __device__ static __forceinline__ C tmul(C v, C w) {

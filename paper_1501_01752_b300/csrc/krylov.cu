@@ -13,11 +13,13 @@
 // i.e. classical Gram-Schmidt with the Daniel-Gragg-Kaufman-Stewart
 // reorthogonalisation test instead of the paper's modified Gram-Schmidt: the
 // j sequential dot/axpy pairs of MGS become two fused passes (four when the
-// test fires), with orthogonality at least as good as MGS.  Dots of FP32
-// vectors sum FP32 products over one tile (2048 values: 8 per thread, then a
-// 32-lane tree) and accumulate the tile sums in FP64; Hessenberg, rotations
-// and residual estimates are FP64.  Reductions across
-// blocks use the last-block-done pattern (atomic counter, no waiting).
+// test fires), with orthogonality at least as good as MGS.  The test can be
+// forced on or off per solve (force 1 / 2): complex64 inner solves, which
+// stop at 1e-4 relative, skip the second pass.  Dots of FP32 vectors sum
+// FP32 products in each thread's registers and across a warp, and the warp
+// sums in FP64; Hessenberg, rotations and residual estimates are FP64.
+// Reductions across blocks use the last-block-done pattern (atomic counter,
+// no waiting).
 #include "kernels.h"
 #include "reduce.cuh"
 
@@ -63,10 +65,14 @@ template <typename R> __device__ __forceinline__ R warp_sum(R v) {
 }
 
 // h_i = <v_i, w> for i < nv and ||w||^2: w is held in registers per tile,
-// every basis vector streamed once.  Products are summed in the basis
-// precision over one tile (EPT per thread, then a 32-lane tree) and the tile
-// sums are accumulated in FP64.
+// every basis vector streamed once.  Each block takes a group of GV basis
+// vectors over a strided set of tiles; every thread accumulates its products
+// in registers (basis precision) over all of its tiles, and the block reduces
+// once at the end (warp tree, then FP64 across warps and blocks).
 constexpr int GV = 8;  // basis vectors per block of k_dots (grid.x = tile blocks x vector groups)
+// values per thread and vector in k_dots: 32 bytes, so that four vectors in
+// flight fit in few registers
+template <typename R> struct EptDots { static constexpr int v = sizeof(R) == 4 ? 4 : 2; };
 
 template <typename R>
 __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict__ V, long long vinst, long long Us,
@@ -74,8 +80,8 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
                                              const int *__restrict__ gate, double *partial, unsigned *counter,
                                              double *out, int ostride, int nblk, const int *__restrict__ jdev) {
   using C = typename Cx<R>::T;
-  constexpr int EPT = Ept<R>::v, NW = KT / 32;
-  __shared__ double wsum[2 * GV + 1][NW];
+  constexpr int EPT = EptDots<R>::v, NW = KT / 32, CH = 4, NA = 2 * GV + 1;
+  __shared__ double wsum[NA][NW];
   __shared__ int am_last;
   const int b = blockIdx.y, blk = blockIdx.x % nblk, grp = blockIdx.x / nblk;
   if (!act[b]) return;
@@ -86,75 +92,46 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
   }
   const int K = 2 * nv + 1, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = grp * GV, i1 = min(nv, i0 + GV), ng = max(0, i1 - i0);   // groups past nv only count in
-  for (int k = threadIdx.x; k < (2 * GV + 1) * NW; k += blockDim.x) (&wsum[0][0])[k] = 0.0;
-  __syncthreads();
   const C *Vb = V + b * vinst;
   const C *W = Vb + (long long)wi * Us;
+  const C *V0 = Vb + (long long)i0 * Us;
   const long long ntiles = (Us + KT * EPT - 1) / (KT * EPT);
+  R acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) acc[k] = 0;
   for (long long t = blk; ng > 0 && t < ntiles; t += nblk) {
     const long long e0 = t * (KT * EPT) + (long long)threadIdx.x * EPT;
-    const bool ok = e0 < Us;
+    if (e0 >= Us) continue;          // Us is a multiple of 64: a thread's EPT values are all in range
     C w[EPT];
-    if (ok) load_ept<C, EPT>(w, W + e0);
-    else
+    load_ept<C, EPT>(w, W + e0);
+    if (grp == 0)
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) w[k] = mk((R)0, (R)0);
-    if (grp == 0) {
-      R n2 = 0;
+      for (int k = 0; k < EPT; ++k) acc[2 * GV] += w[k].x * w[k].x + w[k].y * w[k].y;
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) n2 += w[k].x * w[k].x + w[k].y * w[k].y;
-      n2 = warp_sum(n2);
-      if (lane == 0) wsum[2 * GV][warp] += (double)n2;
-    }
-    int i = 0;
-    for (; i + 4 <= ng; i += 4) {   // four basis vectors in flight per thread
-      C v[4][EPT];
+    for (int c0 = 0; c0 < GV; c0 += CH) {
+      if (c0 < ng) {
+        C v[CH][EPT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (ok) load_ept<C, EPT>(v[u], Vb + (long long)(i0 + i + u) * Us + e0);
-        else
+        for (int u = 0; u < CH; ++u) {
+          if (c0 + u < ng) load_ept<C, EPT>(v[u], V0 + (long long)(c0 + u) * Us + e0);
+          else
 #pragma unroll
-          for (int k = 0; k < EPT; ++k) v[u][k] = mk((R)0, (R)0);
-      }
-      R d[8];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        R re = 0, im = 0;
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-          re += v[u][k].x * w[k].x + v[u][k].y * w[k].y;   // conj(v) w
-          im += v[u][k].x * w[k].y - v[u][k].y * w[k].x;
+            for (int k = 0; k < EPT; ++k) v[u][k] = mk((R)0, (R)0);
         }
-        d[2 * u] = re;
-        d[2 * u + 1] = im;
-      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
+        for (int u = 0; u < CH; ++u)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) d[u] += __shfl_xor_sync(0xffffffffu, d[u], o);
-      if (lane == 0)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) wsum[2 * i + u][warp] += (double)d[u];
-    }
-    for (; i < ng; ++i) {
-      C v[EPT];
-      if (ok) load_ept<C, EPT>(v, Vb + (long long)(i0 + i) * Us + e0);
-      else
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) v[k] = mk((R)0, (R)0);
-      R re = 0, im = 0;
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        re += v[k].x * w[k].x + v[k].y * w[k].y;
-        im += v[k].x * w[k].y - v[k].y * w[k].x;
-      }
-      re = warp_sum(re);
-      im = warp_sum(im);
-      if (lane == 0) {
-        wsum[2 * i][warp] += (double)re;
-        wsum[2 * i + 1][warp] += (double)im;
+          for (int k = 0; k < EPT; ++k) {
+            acc[2 * (c0 + u)] += v[u][k].x * w[k].x + v[u][k].y * w[k].y;       // conj(v) w
+            acc[2 * (c0 + u) + 1] += v[u][k].x * w[k].y - v[u][k].y * w[k].x;
+          }
       }
     }
+  }
+#pragma unroll
+  for (int k = 0; k < NA; ++k) {
+    const R sk = warp_sum(acc[k]);
+    if (lane == 0) wsum[k][warp] = (double)sk;
   }
   __syncthreads();
   // this block's share: dots i0..i1-1 (and ||w||^2 from group 0)

@@ -49,16 +49,13 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__res
   using F = Team8<L0>;
   if (jdev) X += (long long)(*jdev) * jstride;
   constexpr int TS = F::TS, RB = TT / TS;
-  __shared__ C tw[TWN];
   __shared__ C bufs[RB * F::BUF];
   const int b = blockIdx.y;
   if (act && !act[b]) return;
-  for (int i = threadIdx.x; i < TWN; i += blockDim.x) tw[i] = twg[i];
-  __syncthreads();
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
   const Lanes ln(TS);
   C w[8];
-  F::twiddles(w, ln.lane, tw);
+  F::twiddles(w, ln.lane, twg);
   const long long nrows = 3LL * N2 * N1;
   const long long r = (long long)blockIdx.x * RB + ln.team;
   const bool valid = r < nrows;
@@ -89,6 +86,16 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__res
   }
 }
 
+// Plane buffer of pass 2: row r (a z harmonic), column c (a y frequency) at
+// r LY + (c XOR sw(r)), sw(r) = 8 (r & 1) + (r & 6).  Row passes touch 4
+// consecutive rows x 8 consecutive columns per warp, column passes 8
+// consecutive rows x 4 consecutive columns: with the swizzle both spread a
+// warp's 8-byte accesses evenly over the 32 banks (two wavefronts, the
+// minimum), where a padded pitch fixes only one of the two patterns.
+template <int LY> __device__ __forceinline__ int yz_at(int r, int c) {
+  return r * LY + (c ^ (((r & 1) << 3) | (r & 6)));
+}
+
 template <typename R, int LY, int LZ, int TT>
 __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restrict__ T, const R *__restrict__ D,
                                               const int *__restrict__ act, const typename Cx<R>::T *__restrict__ twg) {
@@ -96,21 +103,18 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
   using FY = Team8<LY>;
   using FZ = Team8<LZ>;
   constexpr int NTY = TT / FY::TS, NTZ = TT / FZ::TS, NT = NTY > NTZ ? NTY : NTZ;
-  __shared__ C tw[TWN];
   __shared__ C bufs[NT * FY::BUF];
   extern __shared__ __align__(16) unsigned char sm_dyn[];
-  C *A = reinterpret_cast<C *>(sm_dyn);   // [N2][LY + 1]
+  C *A = reinterpret_cast<C *>(sm_dyn);   // [N2][LY], column index swizzled per row (yz_at)
   const int rx = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   if (act && !act[b]) return;
-  for (int i = threadIdx.x; i < TWN; i += blockDim.x) tw[i] = twg[i];
-  __syncthreads();
-  const int N1 = g.N[1], N2 = g.N[2], PY = LY + 1;
+  const int N1 = g.N[1], N2 = g.N[2];
   C *Tp = T + b * g.Tsz + ((long long)rx * 3 + c) * N2 * N1;   // [m_z][m_y] block
   // y forward: team per m_z row, straight from global memory
   {
     const Lanes ln(FY::TS);
     C w[8];
-    FY::twiddles(w, ln.lane, tw);
+    FY::twiddles(w, ln.lane, twg);
     for (int r0 = 0; r0 < N2; r0 += NTY) {
       const int mz = r0 + ln.team;
       const bool valid = mz < N2;
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
       FY::template forward<+1>(v, ln.lane, w, bufs + ln.team * FY::BUF, ln.mask);
       if (valid)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) A[mz * PY + FY::freq(ln.lane, q)] = v[q];
+        for (int q = 0; q < 8; ++q) A[yz_at<LY>(mz, FY::freq(ln.lane, q))] = v[q];
     }
   }
   __syncthreads();
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
   {
     const Lanes ln(FZ::TS);
     C w[8];
-    FZ::twiddles(w, ln.lane, tw);
+    FZ::twiddles(w, ln.lane, twg);
     const R *Dx = D + (long long)rx * LY * LZ;
     for (int c0 = 0; c0 < LY; c0 += NTZ) {
       const int ry = c0 + ln.team;
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int h = harm_at(ln.lane + FZ::TS * a, g.n[2], LZ);
-        v[a] = (valid && h >= 0) ? A[h * PY + ry] : mk((R)0, (R)0);
+        v[a] = (valid && h >= 0) ? A[yz_at<LY>(h, ry)] : mk((R)0, (R)0);
       }
       C *bf = bufs + ln.team * FZ::BUF;
       FZ::template forward<+1>(v, ln.lane, w, bf, ln.mask);
@@ -158,7 +162,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
           const int h = harm_at(ln.lane + FZ::TS * a, g.n[2], LZ);
-          if (h >= 0) A[h * PY + ry] = v[a];
+          if (h >= 0) A[yz_at<LY>(h, ry)] = v[a];
         }
     }
   }
@@ -167,13 +171,13 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
   {
     const Lanes ln(FY::TS);
     C w[8];
-    FY::twiddles(w, ln.lane, tw);
+    FY::twiddles(w, ln.lane, twg);
     for (int r0 = 0; r0 < N2; r0 += NTY) {
       const int mz = r0 + ln.team;
       const bool valid = mz < N2;
       C v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = valid ? A[mz * PY + FY::freq(ln.lane, q)] : mk((R)0, (R)0);
+      for (int q = 0; q < 8; ++q) v[q] = valid ? A[yz_at<LY>(mz, FY::freq(ln.lane, q))] : mk((R)0, (R)0);
       FY::template inverse<-1>(v, ln.lane, w, bufs + ln.team * FY::BUF, ln.mask);
       if (valid)
 #pragma unroll
@@ -184,6 +188,11 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
     }
   }
 }
+
+// Row pitch of the pass-3 buffer: 8 mod 16 complex values, so the four
+// teams of a warp (consecutive rows, 8 consecutive columns each) cover the
+// 32 banks evenly.
+__host__ __device__ __forceinline__ int p3_pitch(int N0) { return (N0 + 15) / 16 * 16 + 8; }
 
 // MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u)
 template <typename R, int L0, int MODE, int TT>
@@ -201,26 +210,30 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     Y += (long long)(*jdev) * jstride;
   }
   constexpr int TS = F::TS, NTM = TT / TS;
-  __shared__ C tw[TWN];
   __shared__ C bufs[NTM * F::BUF];
   __shared__ double red[32];
   extern __shared__ __align__(16) unsigned char sm_dyn[];
-  C *S3 = reinterpret_cast<C *>(sm_dyn);   // [3][rows][N0 + 1], then kx[N0]
+  C *S3 = reinterpret_cast<C *>(sm_dyn);   // [3][rows][P], then kx[N0], ky[rows], kz[rows]
   const int b = blockIdx.y;
   if (act && !act[b]) return;
-  for (int i = threadIdx.x; i < TWN; i += blockDim.x) tw[i] = twg[i];
-  const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2], P = N0 + 1;
-  R *kxs = reinterpret_cast<R *>(S3 + 3 * rows * P);
-  for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (R)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
-  __syncthreads();
+  const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2], P = p3_pitch(N0);
   const long long Nh = g.Nh;
   const long long r0 = (long long)blockIdx.x * rows;
   const long long left = (long long)N1 * N2 - r0;
   const int nr = (int)(left < rows ? left : rows);
+  R *kxs = reinterpret_cast<R *>(S3 + 3 * rows * P);
+  R *kys = kxs + N0, *kzs = kys + rows;
+  for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (R)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    const long long rr = r0 + i;
+    const int mz = (int)(rr / N1), my = (int)(rr - (long long)mz * N1);
+    kys[i] = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
+    kzs[i] = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
+  }
   {
     const Lanes ln(TS);
     C w[8];
-    F::twiddles(w, ln.lane, tw);
+    F::twiddles(w, ln.lane, twg);
     const int c = ln.team / rows, row = ln.team - c * rows;
     const bool valid = c < 3 && row < nr;
     const C *Tr = T + b * g.Tsz + r0 + row;
@@ -243,17 +256,14 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   const long long h0 = ((long long)g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
   const C *Xb = X + b * xstride;
   C *Yb = Y + b * ystride;
-  double acc = 0;
-  for (int e = threadIdx.x; e < nr * N0; e += blockDim.x) {
-    const int row = e / N0, mx = e - row * N0;
-    const long long rr = r0 + row;
-    const int mz = (int)(rr / N1), my = (int)(rr - (long long)mz * N1);
-    const long long h = rr * N0 + mx;
+  R acc = 0;   // this thread's share of ||y||^2 (a few harmonics), widened once
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  for (int row = warp; row < nr; row += TT / 32)
+  for (int mx = wl; mx < N0; mx += 32) {
+    const long long h = (r0 + row) * N0 + mx;
     const C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
                  u2 = S3[(2 * rows + row) * P + mx];
-    const R kx = kxs[mx];
-    const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
-    const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
+    const R kx = kxs[mx], ky = kys[row], kz = kzs[row];
     const R id = iden[b * Nh + h];
     const R kux = kx * u0.x + ky * u1.x + kz * u2.x, kuy = kx * u0.y + ky * u1.y + kz * u2.y;
     C y0 = Xb[h], y1 = Xb[Nh + h], y2 = Xb[2 * Nh + h];
@@ -274,14 +284,12 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       y1 = mk(a1.x - y1.x, a1.y - y1.y);
       y2 = mk(a2.x - y2.x, a2.y - y2.y);
     }
-    if (norm_out)
-      acc += (double)y0.x * y0.x + (double)y0.y * y0.y + (double)y1.x * y1.x + (double)y1.y * y1.y +
-             (double)y2.x * y2.x + (double)y2.y * y2.y;
+    if (norm_out) acc += y0.x * y0.x + y0.y * y0.y + y1.x * y1.x + y1.y * y1.y + y2.x * y2.x + y2.y * y2.y;
     Yb[h] = y0;
     Yb[Nh + h] = y1;
     Yb[2 * Nh + h] = y2;
   }
-  if (norm_out) last_block_sum(acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
+  if (norm_out) last_block_sum((double)acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
 }
 
 bool reg_path_ok(const Geo &g) {
@@ -314,7 +322,7 @@ template <typename R, int TT>
 static void pass2(const MatvecArgs<R> &a, cudaStream_t st) {
   using C = typename Cx<R>::T;
   const Geo &g = a.g;
-  const size_t smem = sizeof(C) * (size_t)g.N[2] * (g.L[1] + 1);
+  const size_t smem = sizeof(C) * (size_t)g.N[2] * g.L[1];
   dim3 grid(g.L[0], 3, a.B);
 #define GSM_YZ(LY, LZ)                                                                                      \
   cudaFuncSetAttribute(k_yz_t8<R, LY, LZ, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
@@ -331,7 +339,7 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   using C = typename Cx<R>::T;
   const Geo &g = a.g;
   const int rows = p3_rows(g, TT);
-  const size_t smem = sizeof(C) * 3 * (size_t)rows * (g.N[0] + 1) + sizeof(R) * g.N[0] + 16;
+  const size_t smem = sizeof(C) * 3 * (size_t)rows * p3_pitch(g.N[0]) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
   dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);
 #define GSM_P3(L0, M)                                                                                          \
   cudaFuncSetAttribute(k_inv_x_t8<R, L0, M, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
