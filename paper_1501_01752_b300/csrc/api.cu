@@ -35,6 +35,7 @@ struct Level {
   Geo g;
   double *D64 = nullptr;
   float *D32 = nullptr;
+  float2 *D32p = nullptr;   // x-plane pairs of D32 for the packed complex64 pass 2 (or nullptr)
   int tb[2][3] = {{256, 256, 256}, {256, 256, 256}};  // lane-team block sizes per pass, [FP64, complex64]
   bool tuned[2] = {false, false};
 };
@@ -93,6 +94,7 @@ struct gsm_plan_s {
   long long launches = 0;  // kernels issued by this plan
   bool team_only = false;  // GSM_FFT_PATH=team: shared-memory FFTs everywhere
   bool use_graphs = true;  // inner GMRES cycles as one graph launch (GSM_GRAPHS=0 disables)
+  bool no_packed = false;  // GSM_PACKED=0: complex64 pass 2 one x plane per block instead of packed plane pairs
   cudaStream_t cap_st = nullptr;  // private stream used only to capture graphs
   // pinned host staging
   char *pin = nullptr;
@@ -323,6 +325,10 @@ static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
   CK(cudaMemcpyAsync(dc, grid.data(), LL * sizeof(double2), cudaMemcpyHostToDevice, p->st));
   for (int a = 0; a < 3; ++a) CK(launch_fft_axis(dc, g.L[0], g.L[1], g.L[2], a, +1, 1, 0, p->tw64, p->st));
   CK(launch_d_finalize(dc, g, 1.0 / (double)LL, lv.D64, lv.D32, p->st));
+  if (packed_yz_ok(g) && !p->no_packed) {
+    if (!lv.D32p) CK(cudaMalloc(&lv.D32p, (LL / 2) * sizeof(float2)));
+    CK(launch_pair_d(lv.D32, lv.D32p, g, p->st));
+  }
   CK(cudaStreamSynchronize(p->st));
   cudaFree(dc);
   *out = &lv;
@@ -374,7 +380,8 @@ static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a
 // Autotuner of the lane-team product: for each pass, time the block sizes
 // 128, 256 and 512 threads (one warm-up and three timed launches each, CUDA
 // events on the plan's stream) on the batch about to be solved and keep the
-// fastest.  Runs once per level and precision; GSM_AUTOTUNE=0 keeps 256.
+// fastest.  Runs once per level and precision; GSM_AUTOTUNE=0 keeps 256,
+// GSM_BLOCKS="t1,t2,t3" fixes the three sizes.
 template <typename R>
 static cudaError_t autotune(gsm_plan_t *p, Level &lv, const MatvecArgs<R> &base) {
   const int prec = sizeof(R) == 4 ? 1 : 0;
@@ -382,6 +389,14 @@ static cudaError_t autotune(gsm_plan_t *p, Level &lv, const MatvecArgs<R> &base)
   lv.tuned[prec] = true;
   if (const char *at = std::getenv("GSM_AUTOTUNE"))
     if (std::strcmp(at, "0") == 0) return cudaSuccess;
+  if (const char *fb = std::getenv("GSM_BLOCKS")) {   // "t1,t2,t3": fixed block sizes (e.g. to profile one variant)
+    int t[3];
+    if (std::sscanf(fb, "%d,%d,%d", &t[0], &t[1], &t[2]) == 3) {
+      for (int i = 0; i < 3; ++i)
+        if (t[i] == 128 || t[i] == 256 || t[i] == 512) lv.tb[prec][i] = t[i];
+      return cudaSuccess;
+    }
+  }
   MatvecArgs<R> a = base;
   a.scale = nullptr;
   a.write_back = 0;
@@ -549,6 +564,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   mv.B = B;
   mv.T = (C *)w->T;
   mv.D = sizeof(R) == 4 ? (const R *)lv.D32 : (const R *)lv.D64;
+  mv.Dp = sizeof(R) == 4 ? lv.D32p : nullptr;
   mv.act = k.act;
   mv.inst = w->inst;
   mv.iden = sizeof(R) == 4 ? (const R *)w->iden32 : (const R *)w->iden64;
@@ -805,6 +821,8 @@ gsm_status gsm_plan(const gsm_plan_desc *desc, gsm_plan_t **out) {
     p->team_only = fp && std::strcmp(fp, "team") == 0;
     const char *gr = std::getenv("GSM_GRAPHS");
     p->use_graphs = !(gr && std::strcmp(gr, "0") == 0);
+    const char *pk = std::getenv("GSM_PACKED");
+    p->no_packed = pk && std::strcmp(pk, "0") == 0;
   }
   std::vector<double2> t64(TWN_HOST);
   std::vector<float2> t32(TWN_HOST);
@@ -834,6 +852,7 @@ void gsm_plan_destroy(gsm_plan_t *p) {
   for (auto &kv : p->levels) {
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
+    cudaFree(kv.second.D32p);
   }
   for (auto &kv : p->works) {
     kv.second.drop_graphs();
@@ -881,8 +900,10 @@ gsm_status gsm_set_permittivity(gsm_plan_t *p, const double eps_host[2], const g
   for (auto &kv : p->levels) {
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
+    cudaFree(kv.second.D32p);
     kv.second.D64 = nullptr;
     kv.second.D32 = nullptr;
+    kv.second.D32p = nullptr;
   }
   Level *lv;
   return get_level(p, p->d.n_harm, &lv);
@@ -930,6 +951,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.ystride = g.U;
     a.T = (float2 *)w->T;
     a.D = lv->D32;
+    a.Dp = lv->D32p;
     a.inst = w->inst;
     a.iden = w->iden32;
     a.tw = p->tw32;
@@ -954,6 +976,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
   }
   CK(cudaMemcpyAsync(y, yd, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (p->prof.on) p->prof.collect();
   return GSM_OK;
 }
 

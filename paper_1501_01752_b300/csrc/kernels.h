@@ -77,6 +77,7 @@ template <typename R> struct MatvecArgs {
   long long ystride = 0;
   C *T = nullptr;          // intermediate, B * g.Tsz complex
   const R *D = nullptr;    // convolution multiplier [rx][ry][rz]
+  const float2 *Dp = nullptr;  // complex64 only: D as x-plane pairs [rx / 2][ry][rz] (nullptr = unpaired pass 2)
   const R *scale = nullptr;  // per-instance input scale (nullptr = 1)
   int write_back = 0;      // write the scaled input back to X (normalises a Krylov vector)
   const int *act = nullptr;
@@ -98,6 +99,9 @@ template <typename R>
 cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof, const int *tb);
 // one pass (1, 2, 3) with block size tb in {128, 256, 512} (autotuner)
 template <typename R> cudaError_t launch_reg_pass(int pass, int tb, const MatvecArgs<R> &a, cudaStream_t st);
+// x-plane pairs of the complex64 multiplier for the packed pass 2
+cudaError_t launch_pair_d(const float *D, float2 *Dp, const Geo &g, cudaStream_t st);
+bool packed_yz_ok(const Geo &g);
 int matvec_reg_blocks_pass3(const Geo &g);
 int matvec_blocks_pass3(const Geo &g, size_t csize);
 size_t matvec_max_smem(const Geo &g, size_t csize);

@@ -14,6 +14,7 @@
 //   pass 3  k_inv_x_t8 : team per (c, row): L_x -> N_x, then per harmonic
 //                        the Green tensor and y = x - G u (or the residual)
 #include "fft_team8.cuh"
+#include "fft_team8x2.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
 
@@ -194,6 +195,116 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
 // 32 banks evenly.
 __host__ __device__ __forceinline__ int p3_pitch(int N0) { return (N0 + 15) / 16 * 16 + 8; }
 
+// Pass 2 for complex64 with 64-point y and z transforms, two x frequencies
+// (r_x, r_x + 1) per block: every lane runs the transforms of both planes at
+// once in packed FP32 pairs (Team8x2).  The plane buffer holds value pairs
+// at row r, column c ^ (r & 7) (16-byte entries: eight lanes reading a row
+// segment or a column segment hit distinct bank groups).  D comes as plane
+// pairs Dp[r_x / 2][r_y][r_z] = (D(r_x, ...), D(r_x + 1, ...)).
+__device__ __forceinline__ int yz2_at(int r, int c) { return r * 64 + (c ^ (r & 7)); }
+
+template <int TT>
+__global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, const float2 *__restrict__ Dp,
+                                                const int *__restrict__ act, const float2 *__restrict__ twg) {
+  using F = Team8x2;
+  extern __shared__ __align__(16) unsigned char sm_dyn[];
+  const int N1 = g.N[1], N2 = g.N[2];
+  CP *bufs = reinterpret_cast<CP *>(sm_dyn);   // [TT / 8][64]: team transposes
+  CP *A = bufs + (TT / 8) * 64;                // [N2][64] value pairs, swizzled (yz2_at)
+  constexpr int NT = TT / 8;
+  const int xp = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
+  if (act && !act[b]) return;
+  float2 *Ta = T + b * g.Tsz + ((long long)(2 * xp) * 3 + c) * N2 * N1;   // [m_z][m_y] block of r_x = 2 xp
+  float2 *Tb = Ta + 3LL * N2 * N1;                                         // and of r_x = 2 xp + 1
+  const int team = threadIdx.x >> 3, lane = threadIdx.x & 7;
+  const unsigned mask = 0xffu << (threadIdx.x & 24);
+  CP *bf = bufs + team * 64;
+  WP w[8];
+  F::twiddles(w, lane, twg);
+  const CP zero = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  // y forward: team per m_z row of both planes, straight from global memory
+  for (int r0 = 0; r0 < N2; r0 += NT) {
+    const int mz = r0 + team;
+    const bool valid = mz < N2;
+    CP v[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int h = harm_at(lane + 8 * a, g.n[1], 64);
+      v[a] = zero;
+      if (valid && h >= 0) {
+        const float2 xa = Ta[mz * N1 + h], xb = Tb[mz * N1 + h];
+        v[a] = {make_float2(xa.x, xb.x), make_float2(xa.y, xb.y)};
+      }
+    }
+    F::forward<+1>(v, lane, w, bf, mask);
+    if (valid)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) A[yz2_at(mz, F::freq(lane, q))] = v[q];
+  }
+  __syncthreads();
+  // z forward, times D, z inverse: team per y-frequency column
+  const float2 *Dx = Dp + (long long)xp * 64 * 64;
+  for (int c0 = 0; c0 < 64; c0 += NT) {
+    const int ry = c0 + team;
+    CP v[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int h = harm_at(lane + 8 * a, g.n[2], 64);
+      v[a] = h >= 0 ? A[yz2_at(h, ry)] : zero;
+    }
+    F::forward<+1>(v, lane, w, bf, mask);
+    const float2 *Dc = Dx + ry * 64;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 d = __ldg(&Dc[F::freq(lane, q)]);
+      v[q].re = f2::mul(v[q].re, d);
+      v[q].im = f2::mul(v[q].im, d);
+    }
+    F::inverse<-1>(v, lane, w, bf, mask);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int h = harm_at(lane + 8 * a, g.n[2], 64);
+      if (h >= 0) A[yz2_at(h, ry)] = v[a];
+    }
+  }
+  __syncthreads();
+  // y inverse: team per row, straight to global memory
+  for (int r0 = 0; r0 < N2; r0 += NT) {
+    const int mz = r0 + team;
+    const bool valid = mz < N2;
+    CP v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = valid ? A[yz2_at(mz, F::freq(lane, q))] : zero;
+    F::inverse<-1>(v, lane, w, bf, mask);
+    if (valid)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int h = harm_at(lane + 8 * a, g.n[1], 64);
+        if (h >= 0) {
+          Ta[mz * N1 + h] = make_float2(v[a].re.x, v[a].im.x);
+          Tb[mz * N1 + h] = make_float2(v[a].re.y, v[a].im.y);
+        }
+      }
+  }
+}
+
+// Dp[r_x / 2][r_y][r_z] = (D[r_x][r_y][r_z], D[r_x + 1][r_y][r_z])
+__global__ void k_pair_d(const float *__restrict__ D, float2 *__restrict__ Dp, long long plane, long long npairs) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs * plane;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long xp = i / plane, e = i - xp * plane;
+    Dp[i] = make_float2(D[(2 * xp) * plane + e], D[(2 * xp + 1) * plane + e]);
+  }
+}
+
+cudaError_t launch_pair_d(const float *D, float2 *Dp, const Geo &g, cudaStream_t st) {
+  const long long plane = (long long)g.L[1] * g.L[2], npairs = g.L[0] / 2;
+  k_pair_d<<<148 * 4, 256, 0, st>>>(D, Dp, plane, npairs);
+  return cudaGetLastError();
+}
+
+bool packed_yz_ok(const Geo &g) { return g.L[1] == 64 && g.L[2] == 64 && g.L[0] % 2 == 0; }
+
 // MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u)
 template <typename R, int L0, int MODE, int TT>
 __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T *__restrict__ T,
@@ -322,6 +433,15 @@ template <typename R, int TT>
 static void pass2(const MatvecArgs<R> &a, cudaStream_t st) {
   using C = typename Cx<R>::T;
   const Geo &g = a.g;
+  if constexpr (sizeof(R) == 4) {
+    if (a.Dp && packed_yz_ok(g)) {
+      const size_t smem2 = sizeof(CP) * ((size_t)g.N[2] * 64 + (TT / 8) * 64);
+      dim3 grid2(g.L[0] / 2, 3, a.B);
+      cudaFuncSetAttribute(k_yz_t8x2<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+      k_yz_t8x2<TT><<<grid2, TT, smem2, st>>>(g, a.T, a.Dp, a.act, a.tw);
+      return;
+    }
+  }
   const size_t smem = sizeof(C) * (size_t)g.N[2] * g.L[1];
   dim3 grid(g.L[0], 3, a.B);
 #define GSM_YZ(LY, LZ)                                                                                      \
