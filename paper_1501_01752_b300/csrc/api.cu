@@ -621,14 +621,8 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     CK(cudaMemcpy2DAsync(k.gv, (m + 1) * 16, h_g0, 16, 16, B, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(k.kcount, 0, (size_t)B * 4, st));
     // V_0 = r in the basis precision (normalised in place by the first pass 1)
-    for (int b = 0; b < B; ++b) {
-      if (!need[b]) continue;
-      if (prec) {
-        CK(launch_convert_d2f(w->r64 + (size_t)b * g.U, (float2 *)(V + b * vinst), g.U, st));
-        p->launches++;
-      }
-      else CK(cudaMemcpyAsync((double2 *)(V + b * vinst), w->r64 + (size_t)b * g.U, g.U * 16, cudaMemcpyDeviceToDevice, st));
-    }
+    CK(launch_start_basis<C>(w->r64, g.U, V, vinst, g.U, B, k.nblk, w->need, st));
+    p->launches++;
     cudaGraphExec_t cyc = (p->use_graphs && !prof) ? cycle_graph<R>(p, w, lv, mv, k, V, vinst, Us, adj) : nullptr;
     if (cyc) {
       // the whole cycle on the device: steps run until every instance has

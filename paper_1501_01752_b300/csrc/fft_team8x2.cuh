@@ -12,9 +12,10 @@
 // with registers 2..5 zero (harmonics placed at m mod 64 with 64 >= 4n + 4)
 // take the pruned first stage.
 //
-// The team buffer holds 8 x 8 value pairs; entry (row, col) sits at
-// 8 row + (col XOR row), which keeps both the row-wise writes and the
-// column-wise reads of eight lanes on distinct 16-byte bank groups.
+// The team buffer holds 8 x 8 value pairs with a row pitch of 9: the
+// row-wise writes (lane = row) and the column-wise reads (lane = column) of
+// eight lanes then fall on distinct 16-byte bank groups, and every access
+// is a per-lane base address plus a compile-time offset.
 #pragma once
 #include "fft.cuh"
 
@@ -85,6 +86,7 @@ template <int S> __device__ __forceinline__ CP cp_twiddle(CP v, WP w) {
 
 struct Team8x2 {
   static constexpr int L = 64;
+  static constexpr int BUF = 72;   // value pairs per team buffer (8 rows, pitch 9)
   // spectral layout of the forward output: frequency lane + 8 r in register r
   __host__ __device__ static constexpr int freq(int lane, int r) { return lane + 8 * r; }
 
@@ -155,31 +157,62 @@ struct Team8x2 {
     close8<S>(v, E0, E1, E2, E3, O0, O1, O2, O3);
   }
 
+  // outputs 0, 1, 6, 7 of an 8-point DFT (the others are left undefined):
+  // the last stage of an inverse transform whose outputs outside the
+  // harmonic box are not kept
+  template <int S> __device__ static __forceinline__ void dft8_out0167(CP *v) {
+    CP e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    CP o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<S>(e0, e1, e2, e3);
+    dft4<S>(o0, o1, o2, o3);
+    const float h = 0.70710678118654752440f;
+    const float2 H = make_float2(h, h), NH = make_float2(-h, -h);
+    v[0] = cp_add(e0, o0);
+    v[6] = cp_sub_si<S>(e2, o2);
+    const float2 xr = S > 0 ? f2::sub(o1.re, o1.im) : f2::add(o1.re, o1.im);
+    const float2 xi = S > 0 ? f2::add(o1.im, o1.re) : f2::sub(o1.im, o1.re);
+    v[1] = {f2::fma(xr, H, e1.re), f2::fma(xi, H, e1.im)};
+    if (S > 0) {
+      const float2 yr = f2::add(o3.re, o3.im), yi = f2::sub(o3.re, o3.im);
+      v[7] = {f2::fma(yr, H, e3.re), f2::fma(yi, NH, e3.im)};
+    } else {
+      const float2 yr = f2::sub(o3.im, o3.re), yi = f2::add(o3.re, o3.im);
+      v[7] = {f2::fma(yr, NH, e3.re), f2::fma(yi, H, e3.im)};
+    }
+  }
+
   template <int S>
   __device__ static __forceinline__ void forward(CP (&v)[8], int lane, const WP (&w)[8], CP *buf, unsigned mask) {
     dft8_in0167<S>(v);                          // Y[t = lane][p], p = register
 #pragma unroll
     for (int p = 1; p < 8; ++p) v[p] = cp_twiddle<S>(v[p], w[p]);
+    CP *row = buf + lane * 9;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) buf[lane * 8 + (p ^ lane)] = v[p];
+    for (int p = 0; p < 8; ++p) row[p] = v[p];
     __syncwarp(mask);
+    const CP *col = buf + lane;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = buf[t * 8 + (lane ^ t)];   // Y[t][p = lane]
-    dft8<S>(v);                                                  // X[lane + 8 s], s = register
+    for (int t = 0; t < 8; ++t) v[t] = col[t * 9];   // Y[t][p = lane]
+    dft8<S>(v);                                      // X[lane + 8 s], s = register
     __syncwarp(mask);
   }
 
-  template <int S>
+  // inverse from the spectral layout; OUT0167 computes only the natural
+  // positions lane + 8 a with a in {0, 1, 6, 7}
+  template <int S, bool OUT0167 = false>
   __device__ static __forceinline__ void inverse(CP (&v)[8], int lane, const WP (&w)[8], CP *buf, unsigned mask) {
     dft8<S>(v);                                                  // W[p = lane][t], t = register
 #pragma unroll
     for (int t = 1; t < 8; ++t) v[t] = cp_twiddle<S>(v[t], w[t]);   // w_64^{S t p}, p = lane
+    CP *row = buf + lane * 9;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) buf[lane * 8 + (t ^ lane)] = v[t];
+    for (int t = 0; t < 8; ++t) row[t] = v[t];
     __syncwarp(mask);
+    const CP *col = buf + lane;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) v[p] = buf[p * 8 + (lane ^ p)];   // W[p][t = lane]
-    dft8<S>(v);                                                  // x[lane + 8 a], a = register
+    for (int p = 0; p < 8; ++p) v[p] = col[p * 9];               // W[p][t = lane]
+    if (OUT0167) dft8_out0167<S>(v);
+    else dft8<S>(v);                                             // x[lane + 8 a], a = register
     __syncwarp(mask);
   }
 };

@@ -155,6 +155,9 @@ cudaError_t launch_resid_sub(double2 *r64, long long rinst, const float2 *Ad, lo
                              int nblk, const int *need, double *partial, unsigned *counter, double *norm_out,
                              cudaStream_t st);
 template <typename C>
+cudaError_t launch_start_basis(const double2 *r64, long long rinst, C *V, long long vinst, long long U, int B,
+                               int nblk, const int *need, cudaStream_t st);
+template <typename C>
 cudaError_t launch_zero_pads(C *V, long long nvec, long long U, long long Us, cudaStream_t st);
 cudaError_t launch_set_rhs(double2 *r64, long long xinst, const Geo &g, const Inst *inst, int B, cudaStream_t st);
 cudaError_t launch_extract_e0(const double2 *x64, long long xinst, const Geo &g, int B, double2 *out,

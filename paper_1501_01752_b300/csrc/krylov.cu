@@ -224,75 +224,108 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
 }
 
 // Column j of the Hessenberg matrix, Givens rotations, residual estimate
-// (one thread per instance; Saad's GMRES with complex rotations).
-__global__ void k_finish(KrylovPtrs k, int j) {
+// (Saad's GMRES with complex rotations).  One warp per instance: the lanes
+// fetch the column and the earlier rotations into shared memory in
+// parallel, lane 0 applies the rotations in order, and the lanes write the
+// rotated column back.
+constexpr int FIN_W = 4;  // instances (warps) per block of k_finish
+__global__ void __launch_bounds__(32 * FIN_W) k_finish(KrylovPtrs k, int j) {
+  __shared__ double2 col_s[FIN_W][MAXM + 1];
+  __shared__ double cs_s[FIN_W][MAXM];
+  __shared__ double2 sn_s[FIN_W][MAXM];
   if (k.jdev) j = *k.jdev;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= k.B || !k.act[b]) return;
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * FIN_W + wi;
+  if (b >= k.B || !k.act[b]) return;   // uniform over the warp
   const int m = k.m, hs = 2 * (m + 1) + 1;
-  double2 col[MAXM + 1];
   const bool re = k.gate[b] != 0;
   const double *h0 = k.hdot0 + (long long)b * hs, *h1 = k.hdot1 + (long long)b * hs;
-  for (int i = 0; i <= j; ++i) {
-    col[i].x = h0[2 * i] + (re ? h1[2 * i] : 0.0);
-    col[i].y = h0[2 * i + 1] + (re ? h1[2 * i + 1] : 0.0);
-  }
-  const double hn = sqrt(fmax(re ? k.wn1[b] : k.wn0[b], 0.0));
   double *cs = k.cs + (long long)b * m;
   double2 *sn = k.sn + (long long)b * m;
-  double2 *g = k.gv + (long long)b * (m + 1);
-  for (int i = 0; i < j; ++i) {
-    const double2 a = col[i], c2 = col[i + 1];
-    const double c = cs[i];
-    const double2 s = sn[i];
-    col[i] = mk(c * a.x + s.x * c2.x - s.y * c2.y, c * a.y + s.x * c2.y + s.y * c2.x);
-    // -conj(s) a + c c2
-    col[i + 1] = mk(-(s.x * a.x + s.y * a.y) + c * c2.x, -(s.x * a.y - s.y * a.x) + c * c2.y);
+  double2 *col = col_s[wi];
+  for (int i = lane; i <= j; i += 32)
+    col[i] = mk(h0[2 * i] + (re ? h1[2 * i] : 0.0), h0[2 * i + 1] + (re ? h1[2 * i + 1] : 0.0));
+  for (int i = lane; i < j; i += 32) {
+    cs_s[wi][i] = cs[i];
+    sn_s[wi][i] = sn[i];
   }
-  const double2 a = col[j];
-  const double na = hypot(a.x, a.y);
-  const double rho = hypot(na, hn);
-  double c;
-  double2 s;
-  if (na == 0.0) {
-    c = 0.0;
-    s = mk(1.0, 0.0);
-  } else {
-    c = na / rho;
-    s = mk(a.x / na * hn / rho, a.y / na * hn / rho);
+  __syncwarp();
+  if (lane == 0) {
+    const double hn = sqrt(fmax(re ? k.wn1[b] : k.wn0[b], 0.0));
+    double2 *g = k.gv + (long long)b * (m + 1);
+    double2 a = col[0];
+    for (int i = 0; i < j; ++i) {
+      const double2 c2 = col[i + 1];
+      const double c = cs_s[wi][i];
+      const double2 s = sn_s[wi][i];
+      col[i] = mk(c * a.x + s.x * c2.x - s.y * c2.y, c * a.y + s.x * c2.y + s.y * c2.x);
+      // -conj(s) a + c c2
+      a = mk(-(s.x * a.x + s.y * a.y) + c * c2.x, -(s.x * a.y - s.y * a.x) + c * c2.y);
+    }
+    const double na = hypot(a.x, a.y);
+    const double rho = hypot(na, hn);
+    double c;
+    double2 s;
+    if (na == 0.0) {
+      c = 0.0;
+      s = mk(1.0, 0.0);
+    } else {
+      c = na / rho;
+      s = mk(a.x / na * hn / rho, a.y / na * hn / rho);
+    }
+    col[j] = mk(c * a.x + s.x * hn, c * a.y + s.y * hn);
+    const double2 gj = g[j];
+    g[j + 1] = mk(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+    g[j] = mk(c * gj.x, c * gj.y);
+    cs[j] = c;
+    sn[j] = s;
+    k.kcount[b] = j + 1;
+    k.scale32[b] = hn > 0 ? (float)(1.0 / hn) : 0.f;
+    k.scale64[b] = hn > 0 ? 1.0 / hn : 0.0;
+    const double r = hypot(g[j + 1].x, g[j + 1].y);
+    k.resid[b] = r;
+    if (r <= k.thresh[b] || hn == 0.0 || j + 1 >= m) k.act[b] = 0;
   }
-  col[j] = mk(c * a.x + s.x * hn, c * a.y + s.y * hn);
-  const double2 gj = g[j];
-  g[j + 1] = mk(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-  g[j] = mk(c * gj.x, c * gj.y);
-  cs[j] = c;
-  sn[j] = s;
+  __syncwarp();
   double2 *Hc = k.H + ((long long)b * m + j) * (m + 1);
-  for (int i = 0; i <= j; ++i) Hc[i] = col[i];
-  k.kcount[b] = j + 1;
-  k.scale32[b] = hn > 0 ? (float)(1.0 / hn) : 0.f;
-  k.scale64[b] = hn > 0 ? 1.0 / hn : 0.0;
-  const double r = hypot(g[j + 1].x, g[j + 1].y);
-  k.resid[b] = r;
-  if (r <= k.thresh[b] || hn == 0.0 || j + 1 >= m) k.act[b] = 0;
+  for (int i = lane; i <= j; i += 32) Hc[i] = col[i];
 }
 
-// y = R^-1 g over the kcount[b] rotated columns (back substitution).
-__global__ void k_backsolve(KrylovPtrs k) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= k.B) return;
+// y = R^-1 g over the kcount[b] rotated columns (back substitution).  One
+// block per instance: all threads stage the upper triangle (column l at
+// l (l + 1) / 2) in shared memory, then warp 0 substitutes column by
+// column, every lane updating its rows of the right-hand side.
+constexpr int BS_T = 256;
+__global__ void __launch_bounds__(BS_T) k_backsolve(KrylovPtrs k) {
+  extern __shared__ __align__(16) unsigned char bs_dyn[];
+  double2 *Rs = reinterpret_cast<double2 *>(bs_dyn);   // m (m + 1) / 2 entries
+  __shared__ double2 s_s[MAXM];
+  const int b = blockIdx.x;
   const int m = k.m, n = k.kcount[b];
-  const double2 *g = k.gv + (long long)b * (m + 1);
+  const double2 *Hb = k.H + (long long)b * m * (m + 1);
+  const long long tri = (long long)n * (n + 1) / 2;
+  for (long long e = threadIdx.x; e < tri; e += blockDim.x) {
+    // column l holds rows 0..l: e = l (l + 1) / 2 + i
+    int l = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((long long)l * (l + 1) / 2 > e) --l;
+    while ((long long)(l + 1) * (l + 2) / 2 <= e) ++l;
+    const int i = (int)(e - (long long)l * (l + 1) / 2);
+    Rs[e] = Hb[(long long)l * (m + 1) + i];
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_s[i] = k.gv[(long long)b * (m + 1) + i];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   double2 *y = k.y + (long long)b * m;
-  for (int i = n - 1; i >= 0; --i) {
-    double2 s = g[i];
-    for (int l = i + 1; l < n; ++l) {
-      const double2 r = k.H[((long long)b * m + l) * (m + 1) + i];
-      s = csub(s, cmul(r, y[l]));
-    }
-    const double2 d = k.H[((long long)b * m + i) * (m + 1) + i];
+  for (int l = n - 1; l >= 0; --l) {
+    const double2 d = Rs[(long long)l * (l + 1) / 2 + l];
     const double dd = d.x * d.x + d.y * d.y;
-    y[i] = dd > 0 ? mk((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd) : mk(0.0, 0.0);
+    const double2 s = s_s[l];
+    const double2 yl = dd > 0 ? mk((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd) : mk(0.0, 0.0);
+    if (lane == 0) y[l] = yl;
+    const double2 *Rc = Rs + (long long)l * (l + 1) / 2;
+    for (int i = lane; i < l; i += 32) s_s[i] = csub(s_s[i], cmul(Rc[i], yl));
+    __syncwarp();
   }
 }
 
@@ -352,6 +385,32 @@ cudaError_t launch_resid_sub(double2 *r64, long long rinst, const float2 *Ad, lo
   k_resid_sub<<<grid, KT, 0, st>>>(r64, rinst, Ad, ainst, U, need, partial, counter, norm_out);
   return cudaGetLastError();
 }
+
+// V_b[0] = r_b in the basis precision, for every instance that starts a cycle
+template <typename C>
+__global__ void __launch_bounds__(KT) k_start_basis(const double2 *__restrict__ r64, long long rinst, C *__restrict__ V,
+                                                    long long vinst, long long U, const int *__restrict__ need) {
+  const int b = blockIdx.y;
+  if (!need[b]) return;
+  const double2 *rb = r64 + b * rinst;
+  C *vb = V + b * vinst;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < U; e += (long long)gridDim.x * blockDim.x) {
+    const double2 r = rb[e];
+    vb[e] = mk((decltype(vb[0].x))r.x, (decltype(vb[0].x))r.y);
+  }
+}
+
+template <typename C>
+cudaError_t launch_start_basis(const double2 *r64, long long rinst, C *V, long long vinst, long long U, int B,
+                               int nblk, const int *need, cudaStream_t st) {
+  dim3 grid(nblk, B);
+  k_start_basis<C><<<grid, KT, 0, st>>>(r64, rinst, V, vinst, U, need);
+  return cudaGetLastError();
+}
+template cudaError_t launch_start_basis<float2>(const double2 *, long long, float2 *, long long, long long, int, int,
+                                                const int *, cudaStream_t);
+template cudaError_t launch_start_basis<double2>(const double2 *, long long, double2 *, long long, long long, int, int,
+                                                 const int *, cudaStream_t);
 
 // zero the padding (U..Us) of every stored Krylov vector
 template <typename C>
@@ -423,7 +482,7 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
 }
 
 cudaError_t launch_finish(const KrylovPtrs &k, int j, cudaStream_t st) {
-  k_finish<<<(k.B + 31) / 32, 32, 0, st>>>(k, j);
+  k_finish<<<(k.B + FIN_W - 1) / FIN_W, 32 * FIN_W, 0, st>>>(k, j);
   return cudaGetLastError();
 }
 
@@ -448,7 +507,9 @@ cudaError_t launch_advance(const KrylovPtrs &k, cudaGraphConditionalHandle h, cu
 }
 
 cudaError_t launch_backsolve(const KrylovPtrs &k, cudaStream_t st) {
-  k_backsolve<<<(k.B + 31) / 32, 32, 0, st>>>(k);
+  const size_t smem = sizeof(double2) * (size_t)k.m * (k.m + 1) / 2;
+  cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_backsolve<<<k.B, BS_T, smem, st>>>(k);
   return cudaGetLastError();
 }
 

@@ -40,7 +40,10 @@ struct Lanes {
   }
 };
 
-template <typename R, int L0, int TT>
+// Each team transforms RPT rows (RB rows apart), issuing the loads of all of
+// them before the first transform, so that more reads are in flight per
+// thread.
+template <typename R, int L0, int TT, int RPT>
 __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
                                                  typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
                                                  int write_back, const int *__restrict__ act,
@@ -58,32 +61,48 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__res
   C w[8];
   F::twiddles(w, ln.lane, twg);
   const long long nrows = 3LL * N2 * N1;
-  const long long r = (long long)blockIdx.x * RB + ln.team;
-  const bool valid = r < nrows;
+  const long long rbase = (long long)blockIdx.x * RB * RPT + ln.team;
   const R s = scale ? scale[b] : (R)1;
-  C *Xr = X + b * xstride + r * N0;
-  C v[8];
+  C v[RPT][8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
-    v[a] = mk((R)0, (R)0);
-    if (valid && h >= 0) {
-      C x = Xr[h];
-      x.x *= s;
-      x.y *= s;
-      if (write_back) Xr[h] = x;
-      v[a] = x;
+  for (int i = 0; i < RPT; ++i) {
+    const long long r = rbase + (long long)i * RB;
+    const bool valid = r < nrows;
+    C *Xr = X + b * xstride + r * N0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
+      v[i][a] = mk((R)0, (R)0);
+      if (valid && h >= 0) v[i][a] = Xr[h];
     }
   }
-  F::template forward<+1>(v, ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
-  if (!valid) return;
-  const int plane = (int)(r / N1), my = (int)(r - (long long)plane * N1);
-  const int c = plane / N2, mz = plane - c * N2;
-  C *Tb = T + b * g.Tsz + (long long)mz * N1 + my;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int rx = F::freq(ln.lane, q);
-    Tb[((long long)rx * 3 + c) * N2 * N1] = v[q];
+  for (int i = 0; i < RPT; ++i) {
+    const long long r = rbase + (long long)i * RB;
+    const bool valid = r < nrows;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      v[i][a].x *= s;
+      v[i][a].y *= s;
+    }
+    if (write_back && valid) {
+      C *Xr = X + b * xstride + r * N0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
+        if (h >= 0) Xr[h] = v[i][a];
+      }
+    }
+    F::template forward<+1>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
+    if (!valid) continue;
+    const int plane = (int)(r / N1), my = (int)(r - (long long)plane * N1);
+    const int c = plane / N2, mz = plane - c * N2;
+    C *Tb = T + b * g.Tsz + (long long)mz * N1 + my;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int rx = F::freq(ln.lane, q);
+      Tb[((long long)rx * 3 + c) * N2 * N1] = v[i][q];
+    }
   }
 }
 
@@ -198,48 +217,62 @@ __host__ __device__ __forceinline__ int p3_pitch(int N0) { return (N0 + 15) / 16
 // Pass 2 for complex64 with 64-point y and z transforms, two x frequencies
 // (r_x, r_x + 1) per block: every lane runs the transforms of both planes at
 // once in packed FP32 pairs (Team8x2).  The plane buffer holds value pairs
-// at row r, column c ^ (r & 7) (16-byte entries: eight lanes reading a row
-// segment or a column segment hit distinct bank groups).  D comes as plane
-// pairs Dp[r_x / 2][r_y][r_z] = (D(r_x, ...), D(r_x + 1, ...)).
-__device__ __forceinline__ int yz2_at(int r, int c) { return r * 64 + (c ^ (r & 7)); }
+// [m_z][r_y] with a row pitch of 65 pairs: a team writing a row segment (8
+// consecutive columns) and a team reading a column segment (8 consecutive
+// rows, 1040 bytes apart) both hit 8 distinct 16-byte bank groups, and
+// every access is a per-lane base plus a compile-time or loop offset.  D
+// comes as plane pairs Dp[r_x / 2][r_y][r_z] = (D(r_x, ...), D(r_x + 1, ...)).
+// Inputs at lane + 8 a exist only for a in {0, 1, 6, 7} (64 >= 4 n + 4),
+// which is also where the inverse transforms' kept outputs lie.
+constexpr int YZP = 65;   // row pitch (value pairs) of the pass-2 plane buffer
+
+__host__ __device__ constexpr int reg0167(int k) { return k < 2 ? k : k + 4; }
 
 template <int TT>
 __global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, const float2 *__restrict__ Dp,
                                                 const int *__restrict__ act, const float2 *__restrict__ twg) {
   using F = Team8x2;
-  extern __shared__ __align__(16) unsigned char sm_dyn[];
-  const int N1 = g.N[1], N2 = g.N[2];
-  CP *bufs = reinterpret_cast<CP *>(sm_dyn);   // [TT / 8][64]: team transposes
-  CP *A = bufs + (TT / 8) * 64;                // [N2][64] value pairs, swizzled (yz2_at)
   constexpr int NT = TT / 8;
+  extern __shared__ __align__(16) unsigned char sm_dyn[];
+  CP *bufs = reinterpret_cast<CP *>(sm_dyn);   // [NT][F::BUF]: team transposes
+  CP *A = bufs + NT * F::BUF;                  // [N2][YZP] value pairs
+  const int N1 = g.N[1], N2 = g.N[2];
   const int xp = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   if (act && !act[b]) return;
   float2 *Ta = T + b * g.Tsz + ((long long)(2 * xp) * 3 + c) * N2 * N1;   // [m_z][m_y] block of r_x = 2 xp
   float2 *Tb = Ta + 3LL * N2 * N1;                                         // and of r_x = 2 xp + 1
   const int team = threadIdx.x >> 3, lane = threadIdx.x & 7;
   const unsigned mask = 0xffu << (threadIdx.x & 24);
-  CP *bf = bufs + team * 64;
+  CP *bf = bufs + team * F::BUF;
   WP w[8];
   F::twiddles(w, lane, twg);
+  int hy[4], hz[4];   // harmonic held by register reg0167(k) of this lane along y / z, or -1
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    hy[k] = harm_at(lane + 8 * reg0167(k), g.n[1], 64);
+    hz[k] = harm_at(lane + 8 * reg0167(k), g.n[2], 64);
+  }
   const CP zero = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   // y forward: team per m_z row of both planes, straight from global memory
   for (int r0 = 0; r0 < N2; r0 += NT) {
     const int mz = r0 + team;
     const bool valid = mz < N2;
+    const float2 *ra = Ta + mz * N1, *rb = Tb + mz * N1;
     CP v[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int h = harm_at(lane + 8 * a, g.n[1], 64);
-      v[a] = zero;
-      if (valid && h >= 0) {
-        const float2 xa = Ta[mz * N1 + h], xb = Tb[mz * N1 + h];
-        v[a] = {make_float2(xa.x, xb.x), make_float2(xa.y, xb.y)};
-      }
-    }
-    F::forward<+1>(v, lane, w, bf, mask);
-    if (valid)
+    for (int a = 0; a < 8; ++a) v[a] = zero;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) A[yz2_at(mz, F::freq(lane, q))] = v[q];
+    for (int k = 0; k < 4; ++k)
+      if (valid && hy[k] >= 0) {
+        const float2 xa = ra[hy[k]], xb = rb[hy[k]];
+        v[reg0167(k)] = {make_float2(xa.x, xb.x), make_float2(xa.y, xb.y)};
+      }
+    F::forward<+1>(v, lane, w, bf, mask);
+    if (valid) {
+      CP *Ar = A + mz * YZP + lane;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) Ar[8 * q] = v[q];
+    }
   }
   __syncthreads();
   // z forward, times D, z inverse: team per y-frequency column
@@ -248,24 +281,22 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, c
     const int ry = c0 + team;
     CP v[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int h = harm_at(lane + 8 * a, g.n[2], 64);
-      v[a] = h >= 0 ? A[yz2_at(h, ry)] : zero;
-    }
+    for (int a = 0; a < 8; ++a) v[a] = zero;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (hz[k] >= 0) v[reg0167(k)] = A[hz[k] * YZP + ry];
     F::forward<+1>(v, lane, w, bf, mask);
-    const float2 *Dc = Dx + ry * 64;
+    const float2 *Dc = Dx + ry * 64 + lane;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const float2 d = __ldg(&Dc[F::freq(lane, q)]);
+      const float2 d = __ldg(&Dc[8 * q]);
       v[q].re = f2::mul(v[q].re, d);
       v[q].im = f2::mul(v[q].im, d);
     }
-    F::inverse<-1>(v, lane, w, bf, mask);
+    F::inverse<-1, true>(v, lane, w, bf, mask);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int h = harm_at(lane + 8 * a, g.n[2], 64);
-      if (h >= 0) A[yz2_at(h, ry)] = v[a];
-    }
+    for (int k = 0; k < 4; ++k)
+      if (hz[k] >= 0) A[hz[k] * YZP + ry] = v[reg0167(k)];
   }
   __syncthreads();
   // y inverse: team per row, straight to global memory
@@ -273,18 +304,20 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, c
     const int mz = r0 + team;
     const bool valid = mz < N2;
     CP v[8];
+    const CP *Ar = A + mz * YZP + lane;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = valid ? A[yz2_at(mz, F::freq(lane, q))] : zero;
-    F::inverse<-1>(v, lane, w, bf, mask);
-    if (valid)
+    for (int q = 0; q < 8; ++q) v[q] = valid ? Ar[8 * q] : zero;
+    F::inverse<-1, true>(v, lane, w, bf, mask);
+    if (valid) {
+      float2 *ra = Ta + mz * N1, *rb = Tb + mz * N1;
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int h = harm_at(lane + 8 * a, g.n[1], 64);
-        if (h >= 0) {
-          Ta[mz * N1 + h] = make_float2(v[a].re.x, v[a].im.x);
-          Tb[mz * N1 + h] = make_float2(v[a].re.y, v[a].im.y);
+      for (int k = 0; k < 4; ++k)
+        if (hy[k] >= 0) {
+          const CP x = v[reg0167(k)];
+          ra[hy[k]] = make_float2(x.re.x, x.im.x);
+          rb[hy[k]] = make_float2(x.re.y, x.im.y);
         }
-      }
+    }
   }
 }
 
@@ -334,6 +367,29 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   const int nr = (int)(left < rows ? left : rows);
   R *kxs = reinterpret_cast<R *>(S3 + 3 * rows * P);
   R *kys = kxs + N0, *kzs = kys + rows;
+  // epilogue mapping: warp per row (rows warp, warp + NW, ...), lane per
+  // x harmonic (N0 <= 31 on this path since 2 N0 - 1 <= L0 <= 64).  The
+  // first PF rows' inputs are fetched now, so their loads overlap the
+  // transforms below.
+  constexpr int NW = TT / 32, PF = 2;
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  const bool lane_ok = wl < N0;
+  const C *Xb = X + b * xstride;
+  C px[PF][3];
+  R pid[PF];
+#pragma unroll
+  for (int i = 0; i < PF; ++i) {
+    const int row = warp + i * NW;
+    px[i][0] = px[i][1] = px[i][2] = mk((R)0, (R)0);
+    pid[i] = 0;
+    if (lane_ok && row < nr) {
+      const long long h = (r0 + row) * N0 + wl;
+      px[i][0] = Xb[h];
+      px[i][1] = Xb[Nh + h];
+      px[i][2] = Xb[2 * Nh + h];
+      pid[i] = iden[b * Nh + h];
+    }
+  }
   for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (R)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
   for (int i = threadIdx.x; i < nr; i += blockDim.x) {
     const long long rr = r0 + i;
@@ -365,19 +421,15 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   __syncthreads();
   const R kb2 = (R)inst[b].kb2;
   const long long h0 = ((long long)g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
-  const C *Xb = X + b * xstride;
   C *Yb = Y + b * ystride;
   R acc = 0;   // this thread's share of ||y||^2 (a few harmonics), widened once
-  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-  for (int row = warp; row < nr; row += TT / 32)
-  for (int mx = wl; mx < N0; mx += 32) {
+  auto body = [&](int row, C y0, C y1, C y2, R id) {
+    const int mx = wl;
     const long long h = (r0 + row) * N0 + mx;
     const C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
-                 u2 = S3[(2 * rows + row) * P + mx];
+            u2 = S3[(2 * rows + row) * P + mx];
     const R kx = kxs[mx], ky = kys[row], kz = kzs[row];
-    const R id = iden[b * Nh + h];
     const R kux = kx * u0.x + ky * u1.x + kz * u2.x, kuy = kx * u0.y + ky * u1.y + kz * u2.y;
-    C y0 = Xb[h], y1 = Xb[Nh + h], y2 = Xb[2 * Nh + h];
     y0.x -= id * (kb2 * u0.x - kx * kux);
     y0.y -= id * (kb2 * u0.y - kx * kuy);
     y1.x -= id * (kb2 * u1.x - ky * kux);
@@ -399,6 +451,17 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     Yb[h] = y0;
     Yb[Nh + h] = y1;
     Yb[2 * Nh + h] = y2;
+  };
+  if (lane_ok) {
+#pragma unroll
+    for (int i = 0; i < PF; ++i) {
+      const int row = warp + i * NW;
+      if (row < nr) body(row, px[i][0], px[i][1], px[i][2], pid[i]);
+    }
+    for (int row = warp + PF * NW; row < nr; row += NW) {
+      const long long h = (r0 + row) * N0 + wl;
+      body(row, Xb[h], Xb[Nh + h], Xb[2 * Nh + h], iden[b * Nh + h]);
+    }
   }
   if (norm_out) last_block_sum((double)acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
 }
@@ -416,17 +479,19 @@ int matvec_reg_blocks_pass3(const Geo &g) {
   return (int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows);
 }
 
+constexpr int P1_RPT = 2;   // rows per team in pass 1
+
 template <typename R, int TT>
 static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
   const Geo &g = a.g;
-  const int RB = TT / (g.L[0] / 8);
+  const int RB = TT / (g.L[0] / 8) * P1_RPT;
   dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
   if (g.L[0] == 64)
-    k_fwd_x_t8<R, 64, TT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw, a.jdev,
-                                               a.jstride);
+    k_fwd_x_t8<R, 64, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw,
+                                                       a.jdev, a.jstride);
   else
-    k_fwd_x_t8<R, 32, TT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw, a.jdev,
-                                               a.jstride);
+    k_fwd_x_t8<R, 32, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw,
+                                                       a.jdev, a.jstride);
 }
 
 template <typename R, int TT>
@@ -435,7 +500,7 @@ static void pass2(const MatvecArgs<R> &a, cudaStream_t st) {
   const Geo &g = a.g;
   if constexpr (sizeof(R) == 4) {
     if (a.Dp && packed_yz_ok(g)) {
-      const size_t smem2 = sizeof(CP) * ((size_t)g.N[2] * 64 + (TT / 8) * 64);
+      const size_t smem2 = sizeof(CP) * ((size_t)g.N[2] * YZP + (TT / 8) * Team8x2::BUF);
       dim3 grid2(g.L[0] / 2, 3, a.B);
       cudaFuncSetAttribute(k_yz_t8x2<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
       k_yz_t8x2<TT><<<grid2, TT, smem2, st>>>(g, a.T, a.Dp, a.act, a.tw);
