@@ -55,6 +55,14 @@ typedef enum {
 } gsm_status;
 
 enum { GSM_FP64 = 0, GSM_FP32_REFINE = 1 };          /* arithmetic of the solve  */
+/* gsm_apply only: the FP64-accurate product computed in double-float
+ * arithmetic (each real an unevaluated sum of two FP32 values, ~48
+ * significand bits), the arithmetic of the outer residual of refined solves */
+enum { GSM_DF64 = 2 };
+/* outer residual b - A x of GSM_FP32_REFINE solves: double-float on the
+ * FP32 pipes where the lane-team product applies (FFT sizes 32/64), FP64
+ * otherwise (AUTO), or FP64 always */
+enum { GSM_RESID_AUTO = 0, GSM_RESID_FP64 = 1 };
 enum { GSM_GMRES = 0, GSM_BICGSTAB = 1 };            /* Krylov method            */
 enum { GSM_SPHERE = 0, GSM_BOX = 1, GSM_ELLIPSOID = 2 };
 
@@ -77,6 +85,7 @@ typedef struct {
   size_t hbm_cap_bytes; /* 0 = unlimited; bounds the Krylov basis (restart shrinks)      */
   int device;           /* CUDA device ordinal                                           */
   void *cuda_stream;    /* cudaStream_t to issue work on; NULL = default stream          */
+  int residual;         /* GSM_RESID_AUTO or GSM_RESID_FP64 (refined solves)             */
 } gsm_plan_desc;
 
 /* Non-overlapping inclusion in the host medium (GSM section: analytic Fourier
@@ -130,7 +139,9 @@ gsm_status gsm_set_permittivity(gsm_plan_t *plan, const double eps_host[2],
 /* y = A x (Eq. 4 operator, adjoint = 0) or y = A^H x (adjoint = 1) for n
  * points, each x/y of 3 N^3 complex128 (point's truncation).  on_device = 1:
  * x, y are device pointers; 0: host.  precision GSM_FP32_REFINE rounds x to
- * complex64 and applies the FP32 kernels (result widened to complex128). */
+ * complex64 and applies the FP32 kernels (result widened to complex128);
+ * GSM_DF64 applies the double-float kernels (adjoint = 0 and FFT sizes 32
+ * or 64 only, else GSM_ERR_ARG). */
 gsm_status gsm_apply(gsm_plan_t *plan, int n, const gsm_point *points,
                      const double *x, double *y, int on_device, int precision, int adjoint);
 

@@ -12,6 +12,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/gsm.h"
@@ -36,6 +37,7 @@ struct Level {
   double *D64 = nullptr;
   float *D32 = nullptr;
   float2 *D32p = nullptr;   // x-plane pairs of D32 for the packed complex64 pass 2 (or nullptr)
+  dfl *Ddf = nullptr;       // D as double-float, for the outer residual (lane-team levels only)
   int tb[2][3] = {{256, 256, 256}, {256, 256, 256}};  // lane-team block sizes per pass, [FP64, complex64]
   bool tuned[2] = {false, false};
 };
@@ -50,6 +52,7 @@ struct Work {
   double2 *x64 = nullptr, *r64 = nullptr, *T = nullptr, *e0 = nullptr;
   double *iden64 = nullptr;
   float *iden32 = nullptr;
+  dfl *idendf = nullptr;
   Inst *inst = nullptr;
   int *need = nullptr;
   double *mv_partial = nullptr, *mv_norm = nullptr;
@@ -90,6 +93,7 @@ struct gsm_plan_s {
   std::map<Key, Work> works;
   double2 *tw64 = nullptr;
   float2 *tw32 = nullptr;
+  dcx *twdf = nullptr;
   Profiler prof;
   long long launches = 0;  // kernels issued by this plan
   bool team_only = false;  // GSM_FFT_PATH=team: shared-memory FFTs everywhere
@@ -141,6 +145,7 @@ static std::string check_desc(const gsm_plan_desc *d, int L[3]) {
   if (!(d->eps_b[0] > 0)) return "eps_b must be positive";
   if (d->precision != GSM_FP64 && d->precision != GSM_FP32_REFINE) return "precision must be GSM_FP64 or GSM_FP32_REFINE";
   if (d->krylov != GSM_GMRES) return "only GSM_GMRES is implemented";
+  if (d->residual != GSM_RESID_AUTO && d->residual != GSM_RESID_FP64) return "residual must be GSM_RESID_AUTO or GSM_RESID_FP64";
   if (d->restart < 0 || d->restart > 120) return "restart must be in [0, 120]";
   if (d->max_batch < 0 || d->max_batch > 4096) return "max_batch must be in [0, 4096]";
   return "";
@@ -206,6 +211,7 @@ static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nbl
   w.e0 = (double2 *)take((size_t)B * 3 * 16);
   w.iden64 = (double *)take((size_t)B * g.Nh * 8);
   w.iden32 = (float *)take((size_t)B * g.Nh * 4);
+  w.idendf = (dfl *)take((size_t)B * g.Nh * 8);
   w.inst = (Inst *)take((size_t)B * sizeof(Inst));
   w.need = (int *)take((size_t)B * 4);
   const int mvb = std::max(std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8)),
@@ -325,6 +331,10 @@ static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
   CK(cudaMemcpyAsync(dc, grid.data(), LL * sizeof(double2), cudaMemcpyHostToDevice, p->st));
   for (int a = 0; a < 3; ++a) CK(launch_fft_axis(dc, g.L[0], g.L[1], g.L[2], a, +1, 1, 0, p->tw64, p->st));
   CK(launch_d_finalize(dc, g, 1.0 / (double)LL, lv.D64, lv.D32, p->st));
+  if (reg_path_ok(g)) {
+    if (!lv.Ddf) CK(cudaMalloc(&lv.Ddf, LL * sizeof(dfl)));
+    CK(launch_d2df(lv.D64, lv.Ddf, (long long)LL, p->st));
+  }
   if (packed_yz_ok(g) && !p->no_packed) {
     if (!lv.D32p) CK(cudaMalloc(&lv.D32p, (LL / 2) * sizeof(float2)));
     CK(launch_pair_d(lv.D32, lv.D32p, g, p->st));
@@ -372,9 +382,14 @@ static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a
                           cudaStream_t st = nullptr) {
   (void)lv;
   if (!st) st = p->st;
-  if (!p->team_only && a.mode < 2 && reg_path_ok(a.g))
-    return launch_matvec_reg<R>(a, st, prof, lv.tb[sizeof(R) == 4 ? 1 : 0]);
-  return launch_matvec<R>(a, st, prof);
+  if constexpr (std::is_same<R, dfl>::value) {
+    // the double-float product exists only on the lane-team path (callers check)
+    return launch_matvec_reg<dfl>(a, st, prof, nullptr);
+  } else {
+    if (!p->team_only && a.mode < 2 && reg_path_ok(a.g))
+      return launch_matvec_reg<R>(a, st, prof, lv.tb[sizeof(R) == 4 ? 1 : 0]);
+    return launch_matvec<R>(a, st, prof);
+  }
 }
 
 // Autotuner of the lane-team product: for each pass, time the block sizes
@@ -540,7 +555,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   cudaStream_t st = p->st;
   Profiler *prof = p->prof.on ? &p->prof : nullptr;
   CK(cudaMemcpyAsync(w->inst, hI, B * sizeof(Inst), cudaMemcpyHostToDevice, st));
-  CK(launch_iden(g, w->inst, B, w->iden64, w->iden32, st));
+  CK(launch_iden(g, w->inst, B, w->iden64, w->iden32, st, w->idendf));
   CK(cudaMemsetAsync(w->x64, 0, (size_t)B * g.U * 16, st));
   CK(launch_set_rhs(w->r64, g.U, g, w->inst, B, st));
   p->launches += 2;
@@ -591,6 +606,27 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   rs.partial = w->mv_partial;
   rs.counter = w->mv_counter;
   rs.norm_out = w->mv_norm;
+  // the same residual in double-float arithmetic on the FP32 pipes (refined
+  // solves on lane-team levels unless the plan asks for FP64)
+  const bool df_resid = prec && !adj && p->d.residual == GSM_RESID_AUTO && !p->team_only && reg_path_ok(g) &&
+                        lv.Ddf != nullptr;
+  MatvecArgs<dfl> rd;
+  rd.g = g;
+  rd.B = B;
+  rd.X = w->x64;
+  rd.xstride = g.U;
+  rd.Y = w->r64;
+  rd.ystride = g.U;
+  rd.T = reinterpret_cast<dcx *>(w->T);
+  rd.D = lv.Ddf;
+  rd.act = w->need;
+  rd.inst = w->inst;
+  rd.iden = w->idendf;
+  rd.tw = p->twdf;
+  rd.mode = 1;
+  rd.partial = w->mv_partial;
+  rd.counter = w->mv_counter;
+  rd.norm_out = w->mv_norm;
   // block sizes of the lane-team kernels: measured on this batch, first use only
   {
     MatvecArgs<R> tune = mv;
@@ -661,7 +697,8 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     if (!recursive) {
       // FP64 residual of the updated iterate
       if (prof) prof->begin(KIND_RESID64, st);
-      CK(matvec<double>(p, lv, rs, nullptr));
+      if (df_resid) CK(matvec<dfl>(p, lv, rd, nullptr));
+      else CK(matvec<double>(p, lv, rs, nullptr));
       if (prof) prof->end(KIND_RESID64, st, 16.0 * B * (double)(2 * g.U + 2 * g.Tsz) + 8.0 * (double)g.L[0] * g.L[1] * g.L[2]);
       p->launches += 3;
     } else {
@@ -820,19 +857,24 @@ gsm_status gsm_plan(const gsm_plan_desc *desc, gsm_plan_t **out) {
   }
   std::vector<double2> t64(TWN_HOST);
   std::vector<float2> t32(TWN_HOST);
+  std::vector<dcx> tdf(TWN_HOST);
   for (int j = 0; j < TWN_HOST; ++j) {
     const double a = 2.0 * M_PI * j / TWN_HOST;
     t64[j] = make_double2(std::cos(a), std::sin(a));
     t32[j] = make_float2((float)t64[j].x, (float)t64[j].y);
+    tdf[j] = mk(dfl(t64[j].x), dfl(t64[j].y));
   }
   if (cudaMalloc(&p->tw64, sizeof(double2) * TWN_HOST) != cudaSuccess ||
-      cudaMalloc(&p->tw32, sizeof(float2) * TWN_HOST) != cudaSuccess) {
+      cudaMalloc(&p->tw32, sizeof(float2) * TWN_HOST) != cudaSuccess ||
+      cudaMalloc(&p->twdf, sizeof(dcx) * TWN_HOST) != cudaSuccess) {
     cudaGetLastError();
-    if (p->tw64) cudaFree(p->tw64);
+    cudaFree(p->tw64);
+    cudaFree(p->tw32);
     return GSM_ERR_NOMEM;
   }
   if (cudaMemcpy(p->tw64, t64.data(), sizeof(double2) * TWN_HOST, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(p->tw32, t32.data(), sizeof(float2) * TWN_HOST, cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(p->tw32, t32.data(), sizeof(float2) * TWN_HOST, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->twdf, tdf.data(), sizeof(dcx) * TWN_HOST, cudaMemcpyHostToDevice) != cudaSuccess)
     return GSM_ERR_CUDA;
   *out = p.release();
   return GSM_OK;
@@ -847,6 +889,7 @@ void gsm_plan_destroy(gsm_plan_t *p) {
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
     cudaFree(kv.second.D32p);
+    cudaFree(kv.second.Ddf);
   }
   for (auto &kv : p->works) {
     kv.second.drop_graphs();
@@ -855,6 +898,7 @@ void gsm_plan_destroy(gsm_plan_t *p) {
   if (p->cap_st) cudaStreamDestroy(p->cap_st);
   cudaFree(p->tw64);
   cudaFree(p->tw32);
+  cudaFree(p->twdf);
   if (p->pin) cudaFreeHost(p->pin);
   delete p;
 }
@@ -895,6 +939,8 @@ gsm_status gsm_set_permittivity(gsm_plan_t *p, const double eps_host[2], const g
     cudaFree(kv.second.D64);
     cudaFree(kv.second.D32);
     cudaFree(kv.second.D32p);
+    cudaFree(kv.second.Ddf);
+    kv.second.Ddf = nullptr;
     kv.second.D64 = nullptr;
     kv.second.D32 = nullptr;
     kv.second.D32p = nullptr;
@@ -919,6 +965,10 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
   Level *lv;
   if ((s = get_level(p, N, &lv))) return s;
   const Geo &g = lv->g;
+  if (precision != GSM_FP64 && precision != GSM_FP32_REFINE && precision != GSM_DF64)
+    return fail(p, GSM_ERR_ARG, "gsm_apply: unknown precision");
+  if (precision == GSM_DF64 && (adjoint || p->team_only || !reg_path_ok(g) || !lv->Ddf))
+    return fail(p, GSM_ERR_ARG, "gsm_apply: the double-float product needs FFT sizes 32/64 and adjoint = 0");
   const int prec = precision == GSM_FP32_REFINE;
   Work *w;
   if ((s = get_work(p, g, n, 2, 0, &w))) return s;
@@ -928,7 +978,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     if ((s = make_inst(p, points[b], g, hI[b]))) return s;
   cudaStream_t st = p->st;
   CK(cudaMemcpyAsync(w->inst, hI, n * sizeof(Inst), cudaMemcpyHostToDevice, st));
-  CK(launch_iden(g, w->inst, n, w->iden64, w->iden32, st));
+  CK(launch_iden(g, w->inst, n, w->iden64, w->iden32, st, w->idendf));
   const size_t bytes = (size_t)n * g.U * 16;
   double2 *xd = w->x64, *yd = w->r64;
   CK(cudaMemcpyAsync(xd, x, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -952,6 +1002,21 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.mode = adjoint ? 2 : 0;
     CK(matvec<float>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
     CK(launch_convert_f2d(yf, yd, (long long)n * g.U, st));
+  } else if (precision == GSM_DF64) {
+    MatvecArgs<dfl> a;
+    a.g = g;
+    a.B = n;
+    a.X = xd;
+    a.xstride = g.U;
+    a.Y = yd;
+    a.ystride = g.U;
+    a.T = reinterpret_cast<dcx *>(w->T);
+    a.D = lv->Ddf;
+    a.inst = w->inst;
+    a.iden = w->idendf;
+    a.tw = p->twdf;
+    a.mode = 0;
+    CK(matvec<dfl>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
   } else {
     MatvecArgs<double> a;
     a.g = g;

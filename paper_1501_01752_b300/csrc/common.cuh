@@ -24,6 +24,18 @@ template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
 }
 template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
 
+// Element type of the product's input and output vectors in memory (X, Y):
+// the working complex type, except for the double-float product, whose
+// vectors stay complex128 (dfloat.cuh).
+template <typename R> struct Io { using T = typename Cx<R>::T; };
+// conversions at the edges of the product (identity unless specialised)
+template <typename C, typename IO> __device__ __forceinline__ C io_in(IO v) { return v; }
+template <typename IO, typename C> __device__ __forceinline__ IO io_out(C v) { return v; }
+
+// read-only loads of twiddle-table entries
+__device__ __forceinline__ float2 ldg_c(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_c(const double2 *p) { return __ldg(p); }
+
 // Per-instance parameters of one incident point (text after Eq. 4).
 struct Inst {
   double kinc[3];  // k_inc = kappa * kdir

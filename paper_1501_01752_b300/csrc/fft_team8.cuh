@@ -32,7 +32,7 @@ template <int L> struct Team8 {
   // memory (2 or 4 KB: it stays in L1 after the first warps touch it)
   template <typename C> __device__ static __forceinline__ void twiddles(C (&w)[8], int lane, const C *tw) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) w[k] = __ldg(&tw[((lane * k) % L) * (TWN / L)]);
+    for (int k = 0; k < 8; ++k) w[k] = ldg_c(&tw[((lane * k) % L) * (TWN / L)]);
   }
 
   template <int S, typename C> __device__ static __forceinline__ C tmul(C v, C w) {

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace gsm {
 
@@ -69,11 +70,12 @@ struct Profiler {
 
 template <typename R> struct MatvecArgs {
   using C = typename Cx<R>::T;
+  using IO = typename Io<R>::T;
   Geo g;
   int B = 0;
-  C *X = nullptr;          // input field(s), instance stride xstride
+  IO *X = nullptr;         // input field(s), instance stride xstride
   long long xstride = 0;
-  C *Y = nullptr;          // output field(s), instance stride ystride (may equal X only in mode 1? never)
+  IO *Y = nullptr;         // output field(s), instance stride ystride (never aliases X)
   long long ystride = 0;
   C *T = nullptr;          // intermediate, B * g.Tsz complex
   const R *D = nullptr;    // convolution multiplier [rx][ry][rz]
@@ -105,7 +107,9 @@ bool packed_yz_ok(const Geo &g);
 int matvec_reg_blocks_pass3(const Geo &g);
 int matvec_blocks_pass3(const Geo &g, size_t csize);
 size_t matvec_max_smem(const Geo &g, size_t csize);
-cudaError_t launch_iden(const Geo &g, const Inst *inst, int B, double *id64, float *id32, cudaStream_t st);
+cudaError_t launch_iden(const Geo &g, const Inst *inst, int B, double *id64, float *id32, cudaStream_t st,
+                        dfl *iddf = nullptr);
+cudaError_t launch_d2df(const double *in, dfl *out, long long n, cudaStream_t st);
 cudaError_t launch_convert_d2f(const double2 *in, float2 *out, long long n, cudaStream_t st);
 cudaError_t launch_convert_f2d(const float2 *in, double2 *out, long long n, cudaStream_t st);
 

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
 }
 
 // ------------------------------------------------ 1/(k_m^2 - k_b^2) tables
-__global__ void k_iden(Geo g, const Inst *__restrict__ inst, int B, double *id64, float *id32) {
+__global__ void k_iden(Geo g, const Inst *__restrict__ inst, int B, double *id64, float *id32, dfl *iddf) {
   const long long tot = (long long)B * g.Nh;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(e / g.Nh);
@@ -246,7 +246,13 @@ __global__ void k_iden(Geo g, const Inst *__restrict__ inst, int B, double *id64
     const double v = 1.0 / den;
     id64[e] = v;
     id32[e] = (float)v;
+    if (iddf) iddf[e] = dfl(v);
   }
+}
+
+__global__ void k_d2df(const double *__restrict__ in, dfl *__restrict__ out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = dfl(in[e]);
 }
 
 // ------------------------------------------------ precision conversions
@@ -348,10 +354,17 @@ size_t matvec_max_smem(const Geo &g, size_t csize) {
   return p2 > p1 ? p2 : p1;
 }
 
-cudaError_t launch_iden(const Geo &g, const Inst *inst, int B, double *id64, float *id32, cudaStream_t st) {
+cudaError_t launch_iden(const Geo &g, const Inst *inst, int B, double *id64, float *id32, cudaStream_t st,
+                        dfl *iddf) {
   long long tot = (long long)B * g.Nh;
   int blocks = (int)std::min<long long>((tot + 255) / 256, 148 * 16);
-  k_iden<<<blocks, 256, 0, st>>>(g, inst, B, id64, id32);
+  k_iden<<<blocks, 256, 0, st>>>(g, inst, B, id64, id32, iddf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_d2df(const double *in, dfl *out, long long n, cudaStream_t st) {
+  int blocks = (int)std::min<long long>((n + 255) / 256, 148 * 8);
+  k_d2df<<<blocks, 256, 0, st>>>(in, out, n);
   return cudaGetLastError();
 }
 

@@ -44,12 +44,13 @@ struct Lanes {
 // them before the first transform, so that more reads are in flight per
 // thread.
 template <typename R, int L0, int TT, int RPT>
-__global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
+__global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__restrict__ X, long long xstride,
                                                  typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
                                                  int write_back, const int *__restrict__ act,
                                                  const typename Cx<R>::T *__restrict__ twg, const int *__restrict__ jdev,
                                                  long long jstride) {
   using C = typename Cx<R>::T;
+  using IO = typename Io<R>::T;
   using F = Team8<L0>;
   if (jdev) X += (long long)(*jdev) * jstride;
   constexpr int TS = F::TS, RB = TT / TS;
@@ -68,12 +69,12 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__res
   for (int i = 0; i < RPT; ++i) {
     const long long r = rbase + (long long)i * RB;
     const bool valid = r < nrows;
-    C *Xr = X + b * xstride + r * N0;
+    const IO *Xr = X + b * xstride + r * N0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
       v[i][a] = mk((R)0, (R)0);
-      if (valid && h >= 0) v[i][a] = Xr[h];
+      if (valid && h >= 0) v[i][a] = io_in<C>(Xr[h]);
     }
   }
 #pragma unroll
@@ -86,11 +87,11 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Cx<R>::T *__res
       v[i][a].y *= s;
     }
     if (write_back && valid) {
-      C *Xr = X + b * xstride + r * N0;
+      IO *Xr = X + b * xstride + r * N0;
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
-        if (h >= 0) Xr[h] = v[i][a];
+        if (h >= 0) Xr[h] = io_out<IO>(v[i][a]);
       }
     }
     F::template forward<+1>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
@@ -341,13 +342,14 @@ bool packed_yz_ok(const Geo &g) { return g.L[1] == 64 && g.L[2] == 64 && g.L[0] 
 // MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u)
 template <typename R, int L0, int MODE, int TT>
 __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T *__restrict__ T,
-                                                 const typename Cx<R>::T *__restrict__ X, long long xstride,
-                                                 typename Cx<R>::T *__restrict__ Y, long long ystride,
+                                                 const typename Io<R>::T *__restrict__ X, long long xstride,
+                                                 typename Io<R>::T *__restrict__ Y, long long ystride,
                                                  const int *__restrict__ act, const Inst *__restrict__ inst,
                                                  const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,
                                                  int rows, double *partial, unsigned *counter, double *norm_out,
                                                  const int *__restrict__ jdev, long long jstride) {
   using C = typename Cx<R>::T;
+  using IO = typename Io<R>::T;
   using F = Team8<L0>;
   if (jdev) {
     X += (long long)(*jdev) * jstride;
@@ -374,7 +376,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   constexpr int NW = TT / 32, PF = 2;
   const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
   const bool lane_ok = wl < N0;
-  const C *Xb = X + b * xstride;
+  const IO *Xb = X + b * xstride;
   C px[PF][3];
   R pid[PF];
 #pragma unroll
@@ -384,9 +386,9 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     pid[i] = 0;
     if (lane_ok && row < nr) {
       const long long h = (r0 + row) * N0 + wl;
-      px[i][0] = Xb[h];
-      px[i][1] = Xb[Nh + h];
-      px[i][2] = Xb[2 * Nh + h];
+      px[i][0] = io_in<C>(Xb[h]);
+      px[i][1] = io_in<C>(Xb[Nh + h]);
+      px[i][2] = io_in<C>(Xb[2 * Nh + h]);
       pid[i] = iden[b * Nh + h];
     }
   }
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   __syncthreads();
   const R kb2 = (R)inst[b].kb2;
   const long long h0 = ((long long)g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
-  C *Yb = Y + b * ystride;
+  IO *Yb = Y + b * ystride;
   R acc = 0;   // this thread's share of ||y||^2 (a few harmonics), widened once
   auto body = [&](int row, C y0, C y1, C y2, R id) {
     const int mx = wl;
@@ -448,9 +450,9 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       y2 = mk(a2.x - y2.x, a2.y - y2.y);
     }
     if (norm_out) acc += y0.x * y0.x + y0.y * y0.y + y1.x * y1.x + y1.y * y1.y + y2.x * y2.x + y2.y * y2.y;
-    Yb[h] = y0;
-    Yb[Nh + h] = y1;
-    Yb[2 * Nh + h] = y2;
+    Yb[h] = io_out<IO>(y0);
+    Yb[Nh + h] = io_out<IO>(y1);
+    Yb[2 * Nh + h] = io_out<IO>(y2);
   };
   if (lane_ok) {
 #pragma unroll
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     }
     for (int row = warp + PF * NW; row < nr; row += NW) {
       const long long h = (r0 + row) * N0 + wl;
-      body(row, Xb[h], Xb[Nh + h], Xb[2 * Nh + h], iden[b * Nh + h]);
+      body(row, io_in<C>(Xb[h]), io_in<C>(Xb[Nh + h]), io_in<C>(Xb[2 * Nh + h]), iden[b * Nh + h]);
     }
   }
   if (norm_out) last_block_sum((double)acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
@@ -580,5 +582,6 @@ template cudaError_t launch_matvec_reg<float>(const MatvecArgs<float> &, cudaStr
 template cudaError_t launch_matvec_reg<double>(const MatvecArgs<double> &, cudaStream_t, Profiler *, const int *);
 template cudaError_t launch_reg_pass<float>(int, int, const MatvecArgs<float> &, cudaStream_t);
 template cudaError_t launch_reg_pass<double>(int, int, const MatvecArgs<double> &, cudaStream_t);
+template cudaError_t launch_matvec_reg<dfl>(const MatvecArgs<dfl> &, cudaStream_t, Profiler *, const int *);
 
 }  // namespace gsm

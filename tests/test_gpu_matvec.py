@@ -77,3 +77,43 @@ def test_apply_on_device_tensors_and_linearity():
         lhs, rhs = np.vdot(x2[b], ax[b]), np.vdot(ahy[b], x1[b])
         assert abs(lhs - rhs) < 1e-11 * abs(lhs)
     plan.close()
+
+
+# Lane-team cases (every FFT size 32 or 64), where the double-float product
+# exists: ragged rows (N not a multiple of the team width), unequal axes.
+DF_CASES = [c for c in CASES if c[0] in ("woodpile_15", "ellipsoid_21", "woodpile_31", "random_15_21_31",
+                                         "random_21_15_15")]
+
+
+@pytest.mark.parametrize("name,st,n_harm,eps_b,points", DF_CASES, ids=[c[0] for c in DF_CASES])
+def test_double_float_apply_matches_oracle(name, st, n_harm, eps_b, points):
+    # the arithmetic of the outer residual: pairs of FP32 values with ~48
+    # significand bits; an FFT of 64^3 points in it keeps the product within
+    # ~1e-13 of the FP64 oracle (the bound asserted leaves a factor ~10)
+    g = gsm()
+    x = wl.random_field(n_harm, 300 + len(name), batch=len(points))
+    plan = g.plan_for(st, n_harm, eps_b=eps_b, precision=g.FP32_REFINE)
+    ydf = plan.apply(points, x, precision=g.DF64)
+    y64 = plan.apply(points, x, precision=g.FP64)
+    for b, pt in enumerate(points):
+        want = _oracle_apply(st, n_harm, eps_b, pt, x[b], False)
+        assert rel(ydf[b], want) < 1e-12, (name, b, rel(ydf[b], want))
+        assert rel(ydf[b], y64[b]) < 1e-12, (name, b, rel(ydf[b], y64[b]))
+    plan.close()
+
+
+def test_double_float_apply_rejects_other_paths():
+    g = gsm()
+    st = wl.sphere_lattice()
+    plan = g.plan_for(st, (7, 7, 7), precision=g.FP32_REFINE)   # FFT size 16: no lane-team product
+    x = wl.random_field((7, 7, 7), 5)
+    with pytest.raises(g.GsmError) as ei:
+        plan.apply([wl.point(0.8 * K0)], x[None], precision=g.DF64)
+    assert ei.value.status == g.GSM_ERR_ARG
+    plan.close()
+    plan = g.plan_for(wl.woodpile(), (15, 15, 15), precision=g.FP32_REFINE)
+    x = wl.random_field((15, 15, 15), 6)
+    with pytest.raises(g.GsmError) as ei:
+        plan.apply([wl.point(0.8 * K0)], x[None], precision=g.DF64, adjoint=True)
+    assert ei.value.status == g.GSM_ERR_ARG
+    plan.close()

@@ -132,3 +132,27 @@ def test_hbm_cap_restarts_and_still_converges():
     want = _oracle_solve(st, n_harm, 1.0, pt, method="gmres", tol=1e-12)
     assert rel(E, want.ravel()) < 1e-6
     plan.close()
+
+
+@pytest.mark.parametrize("residual", ["auto", "fp64"])
+def test_refined_solve_residual_arithmetic(residual):
+    # the outer residual of a refined solve in double-float (default on
+    # lane-team levels) or FP64: both certify ||b - A x|| <= tol ||b||, checked
+    # here by the oracle's own residual of the returned field
+    g = gsm()
+    st = wl.woodpile()
+    n_harm = (21, 21, 21)
+    pts = wl.woodpile_batch(3)
+    plan = g.plan_for(st, n_harm, precision=g.FP32_REFINE, tol=1e-8,
+                      residual=g.RESID_AUTO if residual == "auto" else g.RESID_FP64)
+    E, infos, s = plan.solve(pts)
+    assert s == 0
+    ost = oracle_structure(st)
+    Delta = ost.delta(n_harm, 1.0)
+    for b, (p, Eb) in enumerate(zip(pts, _fields(plan, pts, E))):
+        kinc = p["kappa"] * np.asarray(p["kdir"])
+        A = oop.Operator(Delta, n_harm, kinc, st["periods"], p["k0"] ** 2)
+        bvec = oop.incident(p["pol"], n_harm)
+        res = np.linalg.norm(bvec - A(Eb.reshape((3,) + n_harm[::-1]))) / np.linalg.norm(bvec)
+        assert infos[b]["rel_residual"] <= 1e-8 and res <= 1.5e-8, (b, res, infos[b])
+    plan.close()
