@@ -33,10 +33,25 @@ METRIC = "solves/s at 31^3 harmonics, residual 1e-8: FP32+refine vs FP64 on B300
 N_HARM = (31, 31, 31)
 TOL = 1e-8
 L2_BYTES = 126 * 1024 * 1024
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
-# from the ncu capture summarised in profiles/ (None until measured for the
-# current kernel version)
-NCU_TRAFFIC = None
+L_FFT = 64
+# Algorithmic bytes of one complex64 product of one instance (the unit of the
+# roofline): read x and write y (3 N^3 complex each), the 3 L^2 N
+# intermediate written and read twice, and the L^3 real multiplier,
+#   B_mv = 8 * 3 (2 N^3 + 4 L^2 N) + 4 L^3 = 14.67 MB at N = 31, L = 64.
+B_MV = 8 * 3 * (2 * N_HARM[0] ** 3 + 4 * L_FFT ** 2 * N_HARM[0]) + 4 * L_FFT ** 3
+# Bytes this implementation's x-first layout actually moves per instance and
+# product (3 L N^2 intermediate): x-forward s_c (U + 3 L N^2), yz pass
+# 2 s_c 3 L N^2, x-inverse + Green s_c (3 L N^2 + 2 U) + 4 N^3, plus the
+# multiplier once per launch.
+_U = 3 * N_HARM[0] ** 3
+_TSZ = 3 * L_FFT * N_HARM[1] * N_HARM[2]
+OWN_MV = 8 * (_U + _TSZ) + 16 * _TSZ + 8 * (_TSZ + 2 * _U) + 4 * N_HARM[0] ** 3
+# dram__bytes_read.sum + dram__bytes_write.sum of the three product kernels
+# for one product launch at the bench batch (128 instances), from the ncu
+# capture summarised in profiles/traffic_c64_product_woodpile31_batch128.md
+# (x-forward 310.8 MB + yz 321.1 MB + x-inverse/Green 366.0 MB); None once a
+# product kernel changes after that capture
+NCU_TRAFFIC = 0.9979e9
 
 
 def peaks():
@@ -269,10 +284,15 @@ def main():
         p64.close()
 
     peak, peak_kind = peaks()
-    # dominant kernel with a byte count (the "other" bucket is bookkeeping)
-    dom = max((k for k in kinds if kinds[k][2] > 0), key=lambda k: kinds[k][1])
-    n, ms, by = kinds[dom]
-    achieved = (by / n) / (ms / n / 1000.0) / 1e9 if n and ms > 0 else 0.0
+    # the complex64 product (x-forward + yz convolution + x-inverse/Green),
+    # timed per kernel with CUDA events on the plan's stream
+    n_mv = kinds["fwd_x"][0]
+    t_mv = sum(kinds[k][1] for k in ("fwd_x", "yz_conv", "inv_x_green")) / max(1, n_mv) / 1000.0   # s per product
+    achieved = B * B_MV / t_mv / 1e9 if t_mv > 0 else 0.0
+    own = (B * OWN_MV + 4 * L_FFT ** 3) / t_mv / 1e9 if t_mv > 0 else 0.0
+    # Gram-Schmidt passes (dots + update), each at its own algorithmic bytes
+    kr_ms = kinds["krylov_dots"][1] + kinds["krylov_update"][1]
+    kr_by = kinds["krylov_dots"][2] + kinds["krylov_update"][2]
     iters = [i["iters"] for i in infos]
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -286,9 +306,15 @@ def main():
         "speedup_vs_fp64": None if fp64_value is None else value / ws / fp64_value,
         "iters_mean": float(np.mean(iters)), "refine_steps_mean": float(np.mean([i["refine_steps"] for i in infos])),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": NCU_TRAFFIC,
-                     "launches": n, "avg_us": 1000.0 * ms / max(1, n)},
+        "roofline": {"kernel": "c64_product (k_fwd_x_t8 + k_yz_t8x2 + k_inv_x_t8)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind + " (copy, burst)", "traffic": NCU_TRAFFIC,
+                     "algorithmic_bytes_per_launch": B * B_MV, "launches": n_mv, "avg_us": 1e6 * t_mv,
+                     "own_layout_GBps": own, "own_layout_frac": own / peak},
+        "roofline_krylov": {"kernel": "k_dots + k_update", "bound": "hbm",
+                            "achieved": kr_by / (kr_ms / 1000.0) / 1e9 if kr_ms > 0 else None,
+                            "peak": peak, "unit": "GB/s",
+                            "frac": (kr_by / (kr_ms / 1000.0) / 1e9) / peak if kr_ms > 0 else None},
         "kernel_shares": {k: {"launches": v[0], "ms": v[1], "GB/s": (v[2] / (v[1] / 1000.0) / 1e9) if v[1] else None}
                           for k, v in kinds.items()},
         "profiled_ms_per_step": 1000 * t_prof / args.steps,
