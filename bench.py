@@ -176,6 +176,8 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="relative tolerance of the complex64 inner GMRES cycles (0 = library default 1e-4)")
     ap.add_argument("--residual", default="auto", choices=["auto", "fp64"],
                     help="outer-residual arithmetic of the refined solve (double-float where available, or FP64)")
     ap.add_argument("--workload", default="woodpile",
@@ -203,7 +205,7 @@ def main():
 
     def make_plan(prec):
         return gsm.plan_for(st, N_HARM, precision=prec, tol=TOL, max_batch=B, device=local,
-                            stream=stream.cuda_stream,
+                            stream=stream.cuda_stream, inner_tol=args.inner_tol,
                             residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO)
 
     plan = make_plan(gsm.FP32_REFINE)

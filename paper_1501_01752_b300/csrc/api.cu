@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -360,17 +361,34 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
   for (int a = 0; a < 3; ++a) I.kinc[a] = pt.kappa * pt.kdir[a] / nrm;
   I.kb2 = pt.k0 * pt.k0 * p->d.eps_b[0];
   for (int i = 0; i < 6; ++i) I.a[i] = pt.pol[i];
-  // Eq. 4 needs k_m^2 != k_b^2 for every harmonic (text after Eq. 4)
-  double kmax2 = 0;
+  // Eq. 4 needs k_m^2 != k_b^2 for every harmonic (text after Eq. 4).  Along
+  // each (m_y, m_z) row, k_m^2 - k_b^2 = (kx0 + m_x K_x)^2 - (k_b^2 - c) is a
+  // parabola in m_x, closest to zero at the one or two m_x nearest the roots
+  // kx = +-sqrt(k_b^2 - c) (or at the vertex when k_b^2 < c): only those are
+  // tested, an O(N^2) scan instead of O(N^3).
+  const double tol = 1e-9 * I.kb2;
   for (int mz = -g.n[2]; mz <= g.n[2]; ++mz)
-    for (int my = -g.n[1]; my <= g.n[1]; ++my)
-      for (int mx = -g.n[0]; mx <= g.n[0]; ++mx) {
-        const double kx = I.kinc[0] + mx * g.K[0], ky = I.kinc[1] + my * g.K[1], kz = I.kinc[2] + mz * g.K[2];
-        const double k2 = kx * kx + ky * ky + kz * kz;
-        if (std::fabs(k2 - I.kb2) <= 1e-9 * I.kb2)
-          return fail(p, GSM_ERR_SINGULAR, "harmonic on the basis light cone (k_m^2 = k_b^2); shift kappa or eps_b");
-        kmax2 = std::max(kmax2, k2);
+    for (int my = -g.n[1]; my <= g.n[1]; ++my) {
+      const double ky = I.kinc[1] + my * g.K[1], kz = I.kinc[2] + mz * g.K[2];
+      const double c = ky * ky + kz * kz, r2 = I.kb2 - c;
+      double targets[2] = {0.0, 0.0};
+      int nt = 1;
+      if (r2 > 0) {
+        targets[0] = std::sqrt(r2);
+        targets[1] = -targets[0];
+        nt = 2;
       }
+      for (int t = 0; t < nt; ++t) {
+        const double mc = (targets[t] - I.kinc[0]) / g.K[0];
+        const int m0 = (int)std::floor(mc);
+        for (int mx = m0 - 1; mx <= m0 + 2; ++mx) {
+          if (mx < -g.n[0] || mx > g.n[0]) continue;
+          const double kx = I.kinc[0] + mx * g.K[0];
+          if (std::fabs(kx * kx + c - I.kb2) <= tol)
+            return fail(p, GSM_ERR_SINGULAR, "harmonic on the basis light cone (k_m^2 = k_b^2); shift kappa or eps_b");
+        }
+      }
+    }
   return GSM_OK;
 }
 
@@ -766,7 +784,8 @@ static gsm_status run_group(gsm_plan_t *p, Level &lv, int B, const gsm_point *pt
 // `sink(point index, level, device field pointer, B-local index)`.
 template <typename F>
 static gsm_status solve_points(gsm_plan_t *p, int n, const gsm_point *points, gsm_info *infos, F sink,
-                               bool adj = false, const double *rhs = nullptr) {
+                               bool adj = false, const double *rhs = nullptr,
+                               const std::function<gsm_status()> &batch_end = nullptr) {
   if (n < 0 || (n > 0 && !points)) return fail(p, GSM_ERR_ARG, "bad point array");
   std::map<Key, std::vector<int>> groups;
   for (int i = 0; i < n; ++i) {
@@ -801,6 +820,8 @@ static gsm_status solve_points(gsm_plan_t *p, int n, const gsm_point *points, gs
         s = sink(idx[off + b], *lv, x + (size_t)b * lv->g.U, b, x);
         if (s) return s;
       }
+      // before the next batch reuses the workspace
+      if (batch_end && (s = batch_end())) return s;
     }
   }
   return worst;
@@ -1051,11 +1072,33 @@ gsm_status gsm_solve(gsm_plan_t *p, int n, const gsm_point *points, double *E, i
     if (s) return s;
     off[i + 1] = off[i] + 3ull * N[0] * N[1] * N[2];
   }
-  gsm_status s = solve_points(p, n, points, infos, [&](int i, Level &lv, double2 *xf, int, double2 *) -> gsm_status {
-    CK(cudaMemcpyAsync(E + 2 * off[i], xf, lv.g.U * 16, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       p->st));
+  // fields that are adjacent both in the workspace and in E leave in one copy
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double *run_dst = nullptr;
+  const double2 *run_src = nullptr;
+  size_t run_bytes = 0;
+  auto flush = [&]() -> gsm_status {
+    if (run_bytes) CK(cudaMemcpyAsync(run_dst, run_src, run_bytes, kind, p->st));
+    run_bytes = 0;
     return GSM_OK;
-  });
+  };
+  gsm_status s = solve_points(
+      p, n, points, infos,
+      [&](int i, Level &lv, double2 *xf, int, double2 *) -> gsm_status {
+        const size_t bytes = lv.g.U * 16;
+        if (run_bytes && (double *)((char *)run_dst + run_bytes) == E + 2 * off[i] &&
+            (const double2 *)((const char *)run_src + run_bytes) == xf) {
+          run_bytes += bytes;
+          return GSM_OK;
+        }
+        gsm_status f = flush();
+        if (f) return f;
+        run_dst = E + 2 * off[i];
+        run_src = xf;
+        run_bytes = bytes;
+        return GSM_OK;
+      },
+      false, nullptr, flush);
   if (s && s != GSM_ERR_NOCONV) return s;
   CK(cudaStreamSynchronize(p->st));
   return s;

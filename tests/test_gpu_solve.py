@@ -156,3 +156,25 @@ def test_refined_solve_residual_arithmetic(residual):
         res = np.linalg.norm(bvec - A(Eb.reshape((3,) + n_harm[::-1]))) / np.linalg.norm(bvec)
         assert infos[b]["rel_residual"] <= 1e-8 and res <= 1.5e-8, (b, res, infos[b])
     plan.close()
+
+
+def test_singular_harmonic_anywhere_in_the_box():
+    # points built so that one harmonic m != 0 lies exactly on the basis
+    # light cone |k_inc + K m|^2 = k_b^2: the plan must refuse them (text
+    # after Eq. 4), and a slightly shifted kappa must solve
+    g = gsm()
+    st = wl.woodpile()
+    n_harm = (9, 9, 9)
+    K = 2 * np.pi / np.asarray(st["periods"])
+    plan = g.plan_for(st, n_harm, precision=g.FP64, tol=1e-10)
+    for m in [(-1, 0, 0), (2, -1, 3), (-4, 4, -4), (0, 3, 0)]:
+        kinc = np.array([K0, 0.0, 0.0]) - K * np.asarray(m)
+        kappa = float(np.linalg.norm(kinc))
+        pt = wl.point(kappa, tuple(kinc / kappa), (0.0, 0.0, 1.0) if m[2] == 0 else (0.0, 1.0, 0.0))
+        with pytest.raises(g.GsmError) as ei:
+            plan.solve([pt])
+        assert ei.value.status == g.GSM_ERR_SINGULAR, m
+        ok = dict(pt, kappa=kappa * (1 + 1e-3))
+        E, infos, s = plan.solve([ok])
+        assert s == 0 and infos[0]["rel_residual"] <= 1e-10, (m, infos)
+    plan.close()
