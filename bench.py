@@ -175,9 +175,13 @@ def main():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--alt-steps", type=int, default=5,
+                    help="timed steps of the other Krylov method on the same batch (0 skips it)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="relative tolerance of the complex64 inner GMRES cycles (0 = library default 1e-4)")
+    ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"],
+                    help="Krylov method of the refined solve (and of the FP64 plain path)")
     ap.add_argument("--residual", default="auto", choices=["auto", "fp64"],
                     help="outer-residual arithmetic of the refined solve (double-float where available, or FP64)")
     ap.add_argument("--workload", default="woodpile",
@@ -206,6 +210,7 @@ def main():
     def make_plan(prec):
         return gsm.plan_for(st, N_HARM, precision=prec, tol=TOL, max_batch=B, device=local,
                             stream=stream.cuda_stream, inner_tol=args.inner_tol,
+                            krylov=gsm.BICGSTAB if args.krylov == "bicgstab" else gsm.GMRES,
                             residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO)
 
     plan = make_plan(gsm.FP32_REFINE)
@@ -276,6 +281,21 @@ def main():
     h2d = B * 88  # instance parameters (kinc, k_b^2, polarisation) per point
     d2h = B * U * 16
 
+    # the other Krylov method on the same batch (few steps; not the headline)
+    alt = "bicgstab" if args.krylov == "gmres" else "gmres"
+    alt_line = None
+    if args.alt_steps > 0:
+        palt = gsm.plan_for(st, N_HARM, precision=gsm.FP32_REFINE, tol=TOL, max_batch=B, device=local,
+                            stream=stream.cuda_stream, inner_tol=args.inner_tol,
+                            krylov=gsm.BICGSTAB if alt == "bicgstab" else gsm.GMRES,
+                            residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO)
+        palt.solve(pts, out=E)
+        talt, infos_alt = timed(palt, args.alt_steps, E)
+        alt_line = {"krylov": alt, "value": B * args.alt_steps / talt, "unit": "solves/s",
+                    "steps": args.alt_steps, "iters_mean": float(np.mean([i["iters"] for i in infos_alt])),
+                    "rel_residual_max": float(max(i["rel_residual"] for i in infos_alt))}
+        palt.close()
+
     # plain FP64 GPU path on the same batch (--fp64-steps 0 skips it)
     fp64_value, infos64 = None, None
     if args.fp64_steps > 0:
@@ -286,38 +306,59 @@ def main():
         p64.close()
 
     peak, peak_kind = peaks()
-    # the complex64 product (x-forward + yz convolution + x-inverse/Green),
-    # timed per kernel with CUDA events on the plan's stream
-    n_mv = kinds["fwd_x"][0]
-    t_mv = sum(kinds[k][1] for k in ("fwd_x", "yz_conv", "inv_x_green")) / max(1, n_mv) / 1000.0   # s per product
+    # The complex64 product (x-forward + yz convolution + x-inverse/Green) on
+    # the full batch with every instance active: R products through gsm_apply,
+    # each pass timed with CUDA events on the plan's stream.  (Inside a solve,
+    # instances that have converged are masked, so a launch there moves less
+    # than B instances' bytes.)
+    xd = torch.from_numpy(wl.random_field(N_HARM, 11, batch=B)).to(dev)
+    plan.apply(pts, xd, precision=gsm.FP32_REFINE)
+    plan.profile(True)
+    R_MV = 5
+    for _ in range(R_MV):
+        plan.apply(pts, xd, precision=gsm.FP32_REFINE)
+    torch.cuda.synchronize()
+    mvk = {name: plan.profile_get(k) for k, name in enumerate(["fwd_x", "yz_conv", "inv_x_green"])}
+    plan.profile(False)
+    n_mv = mvk["fwd_x"][0]
+    t_mv = sum(v[1] for v in mvk.values()) / max(1, n_mv) / 1000.0   # s per product
     achieved = B * B_MV / t_mv / 1e9 if t_mv > 0 else 0.0
     own = (B * OWN_MV + 4 * L_FFT ** 3) / t_mv / 1e9 if t_mv > 0 else 0.0
-    # Gram-Schmidt passes (dots + update), each at its own algorithmic bytes
+    # Gram-Schmidt passes (dots + update) inside the profiled solve, at the
+    # algorithmic bytes of all B instances per launch: an upper bound, since
+    # instances that converged earlier are masked (the smallest active share
+    # of the batch is about mean / max iterations)
     kr_ms = kinds["krylov_dots"][1] + kinds["krylov_update"][1]
     kr_by = kinds["krylov_dots"][2] + kinds["krylov_update"][2]
     iters = [i["iters"] for i in infos]
+    tot_ms = sum(v[1] for v in kinds.values())
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec + c128 refinement", "data": "synthetic",
         "config": {"workload": "woodpile eps 11.9 in eps_b 1, Lambda 0.35, 31^3 harmonics, 64^3 FFT grid",
-                   "global_batch": B * ws, "tol": TOL, "l2": "flushed between steps (inputs+basis > L2)",
+                   "global_batch": B * ws, "tol": TOL, "krylov": args.krylov,
+                   "l2": "flushed between steps (inputs+basis > L2)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "fp64_plain": None if fp64_value is None else
         {"value": fp64_value, "unit": "solves/s", "iters_mean": float(np.mean([i["iters"] for i in infos64]))},
         "speedup_vs_fp64": None if fp64_value is None else value / ws / fp64_value,
+        "alt_krylov": alt_line,
         "iters_mean": float(np.mean(iters)), "refine_steps_mean": float(np.mean([i["refine_steps"] for i in infos])),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "roofline": {"kernel": "c64_product (k_fwd_x_t8 + k_yz_t8x2 + k_inv_x_t8)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind + " (copy, burst)", "traffic": NCU_TRAFFIC,
                      "algorithmic_bytes_per_launch": B * B_MV, "launches": n_mv, "avg_us": 1e6 * t_mv,
+                     "passes_us": {k: 1000.0 * v[1] / max(1, v[0]) for k, v in mvk.items()},
                      "own_layout_GBps": own, "own_layout_frac": own / peak},
         "roofline_krylov": {"kernel": "k_dots + k_update", "bound": "hbm",
                             "achieved": kr_by / (kr_ms / 1000.0) / 1e9 if kr_ms > 0 else None,
                             "peak": peak, "unit": "GB/s",
-                            "frac": (kr_by / (kr_ms / 1000.0) / 1e9) / peak if kr_ms > 0 else None},
-        "kernel_shares": {k: {"launches": v[0], "ms": v[1], "GB/s": (v[2] / (v[1] / 1000.0) / 1e9) if v[1] else None}
+                            "frac": (kr_by / (kr_ms / 1000.0) / 1e9) / peak if kr_ms > 0 else None,
+                            "bound_kind": "upper (masked instances counted)",
+                            "active_share_min": float(np.mean(iters) / max(iters))},
+        "kernel_shares": {k: {"launches": v[0], "ms": v[1], "share": v[1] / tot_ms if tot_ms else None}
                           for k, v in kinds.items()},
         "profiled_ms_per_step": 1000 * t_prof / args.steps,
         "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

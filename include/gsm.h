@@ -76,8 +76,9 @@ typedef struct {
   int fft[3];           /* FFT points per axis; 0 = smallest power of two >= 2N-1 (<= 256) */
   double eps_b[2];      /* basis permittivity eps_b (re, im); im must be 0               */
   int precision;        /* GSM_FP64 or GSM_FP32_REFINE                                   */
-  int krylov;           /* GSM_GMRES (BiCGSTAB: GSM_BICGSTAB)                            */
-  int restart;          /* Krylov basis length m; 0 = 60                                 */
+  int krylov;           /* GSM_GMRES (basis of restart + 1 vectors per instance) or
+                           GSM_BICGSTAB (seven vectors per instance, no restart)          */
+  int restart;          /* GMRES basis length m; 0 = 60                                  */
   int max_iter;         /* total matrix-vector products per instance; 0 = 2000           */
   double tol;           /* target ||b - A x|| / ||b||; 0 = 1e-8                          */
   double inner_tol;     /* FP32 inner GMRES relative tolerance; 0 = 1e-4                 */

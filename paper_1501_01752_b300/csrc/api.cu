@@ -145,7 +145,7 @@ static std::string check_desc(const gsm_plan_desc *d, int L[3]) {
   if (d->eps_b[1] != 0.0) return "complex eps_b is not supported (lossless basis only)";
   if (!(d->eps_b[0] > 0)) return "eps_b must be positive";
   if (d->precision != GSM_FP64 && d->precision != GSM_FP32_REFINE) return "precision must be GSM_FP64 or GSM_FP32_REFINE";
-  if (d->krylov != GSM_GMRES) return "only GSM_GMRES is implemented";
+  if (d->krylov != GSM_GMRES && d->krylov != GSM_BICGSTAB) return "krylov must be GSM_GMRES or GSM_BICGSTAB";
   if (d->residual != GSM_RESID_AUTO && d->residual != GSM_RESID_FP64) return "residual must be GSM_RESID_AUTO or GSM_RESID_FP64";
   if (d->restart < 0 || d->restart > 120) return "restart must be in [0, 120]";
   if (d->max_batch < 0 || d->max_batch > 4096) return "max_batch must be in [0, 4096]";
@@ -525,6 +525,116 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
   return exec;
 }
 
+// One BiCGSTAB iteration (two products and five vector kernels) for the
+// active instances of a batch.
+template <typename R>
+static cudaError_t bicg_iteration(gsm_plan_t *p, const Level &lv, MatvecArgs<R> mv, const BicgPtrs &bp,
+                                  typename Cx<R>::T *V, long long vinst, long long Us, Profiler *prof,
+                                  cudaStream_t st) {
+  using C = typename Cx<R>::T;
+  const double vb = (double)sizeof(C) * bp.U * bp.B;   // bytes per vector of the batch
+  auto step = [&](int which, int kind, double nvec) -> cudaError_t {
+    if (prof) prof->begin(kind, st);
+    cudaError_t e = launch_bicg_step<R>(which, bp, V, vinst, st);
+    if (prof) prof->end(kind, st, vb * nvec);
+    return e;
+  };
+  cudaError_t e;
+  if ((e = step(BICG_P, KIND_UPDATE, 4)) != cudaSuccess) return e;
+  mv.X = V + BS_P * Us;
+  mv.Y = V + BS_V * Us;
+  if ((e = matvec<R>(p, lv, mv, prof, st)) != cudaSuccess) return e;
+  if ((e = step(BICG_ALPHA, KIND_DOTS, 2)) != cudaSuccess) return e;
+  if ((e = step(BICG_S, KIND_UPDATE, 3)) != cudaSuccess) return e;
+  mv.X = V + BS_S * Us;
+  mv.Y = V + BS_T * Us;
+  if ((e = matvec<R>(p, lv, mv, prof, st)) != cudaSuccess) return e;
+  if ((e = step(BICG_OMEGA, KIND_DOTS, 2)) != cudaSuccess) return e;
+  return step(BICG_UPDATE, KIND_UPDATE, 7);
+}
+
+// One BiCGSTAB cycle on r = V[.][BS_R]: r^ = r, d = 0, then iterations until
+// every instance has met its threshold, broken down or hit the iteration
+// cap.  With graphs the loop is a WHILE conditional node (k_bicg_advance sets
+// the condition), built once per workspace; otherwise the host checks the
+// flags every 4 iterations.
+template <typename R>
+static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const MatvecArgs<R> &mv0, const BicgPtrs &bp,
+                              typename Cx<R>::T *V, long long vinst, long long Us, bool adj, Profiler *prof,
+                              int *h_act, cudaGraphExec_t *used) {
+  cudaStream_t st = p->st;
+  MatvecArgs<R> mv = mv0;
+  mv.scale = nullptr;
+  mv.write_back = 0;
+  mv.jdev = nullptr;
+  mv.mode = adj ? 2 : 0;
+  cudaError_t e = launch_bicg_step<R>(BICG_INIT, bp, V, vinst, st);
+  if (e != cudaSuccess) return e;
+  p->launches++;
+  *used = nullptr;
+  const int prec = sizeof(R) == 4;
+  if (p->use_graphs && !prof) {
+    cudaGraphExec_t exec = nullptr;
+    for (auto &c : w->cycles)
+      if (c.B == bp.B && c.m == BS_COUNT - 1 && c.adj == (int)adj && c.force == -1 && c.prec == prec) exec = c.exec;
+    if (!exec) {
+      if (!p->cap_st && cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+      } else {
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+        cudaGraphConditionalHandle h{};
+        cudaGraphNodeParams np{};
+        cudaGraphNode_t node;
+        ok = ok && cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        if (ok) {
+          np.type = cudaGraphNodeTypeConditional;
+          np.conditional.handle = h;
+          np.conditional.type = cudaGraphCondTypeWhile;
+          np.conditional.size = 1;
+          ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+        }
+        if (ok) {
+          cudaGraph_t body = np.conditional.phGraph_out[0];
+          ok = cudaStreamBeginCaptureToGraph(p->cap_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+               cudaSuccess;
+          if (ok) {
+            bool launched = bicg_iteration<R>(p, lv, mv, bp, V, vinst, Us, nullptr, p->cap_st) == cudaSuccess &&
+                            launch_bicg_advance(bp, h, p->cap_st) == cudaSuccess;
+            cudaGraph_t out = nullptr;
+            ok = cudaStreamEndCapture(p->cap_st, &out) == cudaSuccess && launched;
+          }
+        }
+        ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (!ok) {
+          cudaGetLastError();
+          if (graph) cudaGraphDestroy(graph);
+          exec = nullptr;
+        } else {
+          w->cycles.push_back({bp.B, BS_COUNT - 1, (int)adj, -1, prec, graph, exec});
+        }
+      }
+    }
+    if (exec) {
+      *used = exec;
+      return cudaGraphLaunch(exec, st);
+    }
+  }
+  constexpr int CHECK = 4;
+  for (int it = 0; it < bp.max_it; ++it) {
+    if ((e = bicg_iteration<R>(p, lv, mv, bp, V, vinst, Us, prof, st)) != cudaSuccess) return e;
+    p->launches += 2 * 3 + 5;
+    if ((it + 1) % CHECK == 0) {
+      if ((e = cudaMemcpyAsync(h_act, bp.act, bp.B * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+      bool live = false;
+      for (int b = 0; b < bp.B; ++b) live |= h_act[b] != 0;
+      if (!live) break;
+    }
+  }
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------------------ solve
 // Solve A x = b (adj = false) or A^H x = b (adj = true) for B instances of
 // one level.  b = a at m = 0, with a the point's polarisation or, when rhs is
@@ -535,8 +645,12 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   using C = typename Cx<R>::T;
   const Geo &g = lv.g;
   const int prec = sizeof(R) == 4 ? 1 : 0;
-  const int m = capped_restart(p->d, g, B, prec);
+  const bool bicg = p->d.krylov == GSM_BICGSTAB;
+  // GMRES keeps m + 1 basis vectors per instance, BiCGSTAB seven (slots BS_*)
+  const int m = bicg ? BS_COUNT - 1 : capped_restart(p->d, g, B, prec);
   if (m < 2) return fail(p, GSM_ERR_NOMEM, "hbm_cap_bytes leaves fewer than 3 Krylov vectors");
+  if (bicg && p->d.hbm_cap_bytes && (size_t)BS_COUNT * g.U * (prec ? 8 : 16) * B > p->d.hbm_cap_bytes)
+    return fail(p, GSM_ERR_NOMEM, "hbm_cap_bytes is below the 7 BiCGSTAB vectors of the batch");
   Work *w;
   gsm_status s = get_work(p, g, B, m, prec, &w);
   if (s) return s;
@@ -550,6 +664,21 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   // DGKS test.  GSM_REORTH = 0 (test) / 1 (always) / 2 (never) overrides.
   k.force_reorth = (prec && inner_tol_of(p->d) >= 1e-6) ? 2 : 0;
   if (const char *ro = std::getenv("GSM_REORTH")) k.force_reorth = std::atoi(ro);
+  // BiCGSTAB scalars live in the GMRES per-instance arrays (gv has room for 4
+  // complex values per instance, partial for 3 sums per block)
+  BicgPtrs bp;
+  bp.B = B;
+  bp.U = g.U;
+  bp.Us = padded(g.U);
+  bp.nblk = k.nblk;
+  bp.partial = k.partial;
+  bp.counter = k.counter;
+  bp.sc = k.gv;
+  bp.rn2 = k.resid;
+  bp.thresh2 = k.thresh;
+  bp.act = k.act;
+  bp.it = k.kcount;
+  bp.max_it = std::max(1, std::min(1000, (max_iter_of(p->d) + 1) / 2));
   // pinned staging: instance parameters and the small per-cycle arrays
   auto al = [](size_t n) { return (n + 63) & ~(size_t)63; };
   const size_t stage =
@@ -662,6 +791,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     for (int b = 0; b < B; ++b) {
       h_act[b] = need[b];
       h_thr[b] = prec ? itol * rnorm[b] : 0.5 * tol * bnorm[b];
+      if (bicg) h_thr[b] *= h_thr[b];   // BiCGSTAB tests ||r||^2
       h_s32[b] = need[b] ? (float)(1.0 / rnorm[b]) : 0.f;
       h_s64[b] = need[b] ? 1.0 / rnorm[b] : 0.0;
       h_g0[b] = make_double2(rnorm[b], 0.0);
@@ -669,15 +799,29 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     CK(cudaMemcpyAsync(k.act, h_act, B * 4, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(w->need, h_act, B * 4, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(k.thresh, h_thr, B * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(k.scale32, h_s32, B * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(k.scale64, h_s64, B * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(k.gv, 0, (size_t)B * (m + 1) * 16, st));
-    CK(cudaMemcpy2DAsync(k.gv, (m + 1) * 16, h_g0, 16, 16, B, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(k.kcount, 0, (size_t)B * 4, st));
-    // V_0 = r in the basis precision (normalised in place by the first pass 1)
+    if (!bicg) {
+      CK(cudaMemcpyAsync(k.scale32, h_s32, B * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(k.scale64, h_s64, B * 8, cudaMemcpyHostToDevice, st));
+      CK(cudaMemsetAsync(k.gv, 0, (size_t)B * (m + 1) * 16, st));
+      CK(cudaMemcpy2DAsync(k.gv, (m + 1) * 16, h_g0, 16, 16, B, cudaMemcpyHostToDevice, st));
+      CK(cudaMemsetAsync(k.kcount, 0, (size_t)B * 4, st));
+    }
+    // V_0 = r in the basis precision (GMRES normalises it in place in the
+    // first pass 1; it is BiCGSTAB's r_0 as it stands)
     CK(launch_start_basis<C>(w->r64, g.U, V, vinst, g.U, B, k.nblk, w->need, st));
     p->launches++;
-    cudaGraphExec_t cyc = (p->use_graphs && !prof) ? cycle_graph<R>(p, w, lv, mv, k, V, vinst, Us, adj) : nullptr;
+    // complex64 solves keep the correction d (GMRES: in the last basis slot)
+    // when the residual will be updated as r -= A d (see below)
+    bool recursive = prec && outer > 0;
+    for (int b = 0; b < B; ++b)
+      if (need[b] && !cert_ok[b]) recursive = false;
+    cudaGraphExec_t cyc = nullptr;
+    if (bicg) {
+      CK(bicg_cycle<R>(p, w, lv, mv, bp, V, vinst, Us, adj, prof, h_act, &cyc));
+      CK(launch_bicg_sol<R>(w->x64, g.U, V, vinst, bp, w->need, st));
+      p->launches++;
+    } else {
+    cyc = (p->use_graphs && !prof) ? cycle_graph<R>(p, w, lv, mv, k, V, vinst, Us, adj) : nullptr;
     if (cyc) {
       // the whole cycle on the device: steps run until every instance has
       // converged or the basis is full
@@ -704,14 +848,10 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       }
     }
     CK(launch_backsolve(k, st));
-    // complex64 solves keep the correction d in the last basis slot when the
-    // residual will be updated as r -= A d (see below)
-    bool recursive = prec && outer > 0;
-    for (int b = 0; b < B; ++b)
-      if (need[b] && !cert_ok[b]) recursive = false;
     CK(launch_sol_update<R>(k, w->x64, g.U, V, vinst, w->need, recursive ? m : -1, st, prof));
-    CK(cudaMemcpyAsync(h_kc, k.kcount, B * 4, cudaMemcpyDeviceToHost, st));
     p->launches += 2;
+    }
+    CK(cudaMemcpyAsync(h_kc, k.kcount, B * 4, cudaMemcpyDeviceToHost, st));
     if (!recursive) {
       // FP64 residual of the updated iterate
       if (prof) prof->begin(KIND_RESID64, st);
@@ -723,7 +863,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       // r -= A d: A d in complex64 has error ~ eps_mv ||A d|| ~ eps_mv ||r_prev||,
       // far below tol ||b|| once a certified ||r|| <= 1e-3 ||b|| (cert_ok)
       MatvecArgs<R> md = mv;
-      md.X = V + (long long)m * Us;
+      md.X = V + (long long)(bicg ? (int)BS_D : m) * Us;
       md.Y = V;
       md.scale = nullptr;
       md.write_back = 0;
@@ -740,12 +880,12 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     if (cyc) {
       int steps_run = 0;
       for (int b = 0; b < B; ++b) steps_run = std::max(steps_run, need[b] ? h_kc[b] : 0);
-      p->launches += (long long)steps_run * (3 + (k.force_reorth == 2 ? 2 : 4) + 2);
+      p->launches += (long long)steps_run * (bicg ? 2 * 3 + 5 + 1 : 3 + (k.force_reorth == 2 ? 2 : 4) + 2);
     }
     for (int b = 0; b < B; ++b) {
       if (!need[b]) continue;
       steps[b]++;
-      iters[b] += h_kc[b];
+      iters[b] += bicg ? 2 * h_kc[b] : h_kc[b];   // matrix-vector products
       rnorm[b] = std::sqrt(std::max(h_rn[b], 0.0));
       if (!recursive) cert_ok[b] = rnorm[b] <= 1e-3 * bnorm[b];
       if (!std::isfinite(rnorm[b])) {

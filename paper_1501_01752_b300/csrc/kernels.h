@@ -167,6 +167,31 @@ cudaError_t launch_set_rhs(double2 *r64, long long xinst, const Geo &g, const In
 cudaError_t launch_extract_e0(const double2 *x64, long long xinst, const Geo &g, int B, double2 *out,
                               cudaStream_t st);
 
+// BiCGSTAB (bicgstab.cu): seven vectors per instance in the working
+// precision, scalars in FP64.  Slots of V[b][slot][Us]:
+enum { BS_R = 0, BS_RH = 1, BS_P = 2, BS_V = 3, BS_S = 4, BS_T = 5, BS_D = 6, BS_COUNT = 7 };
+// kernels of one iteration, in order (BICG_INIT once per cycle)
+enum { BICG_INIT = 0, BICG_P = 1, BICG_ALPHA = 2, BICG_S = 3, BICG_OMEGA = 4, BICG_UPDATE = 5 };
+struct BicgPtrs {
+  int B;
+  long long U, Us;          // logical and stored vector length
+  int nblk;                 // blocks per instance
+  double *partial;          // [B][nblk][3] block partial sums
+  unsigned *counter;        // [B] last-block counters (zero between kernels)
+  double2 *sc;              // [B][4] rho, rho_old, alpha, omega
+  double *rn2;              // [B] ||r||^2 of the inner residual
+  double *thresh2;          // [B] stop when ||r||^2 <= thresh2
+  int *act;                 // [B] instance still iterating
+  int *it;                  // [B] iterations of this cycle
+  int max_it;               // iteration cap of a cycle
+};
+template <typename R>
+cudaError_t launch_bicg_step(int which, const BicgPtrs &bp, typename Cx<R>::T *V, long long vinst, cudaStream_t st);
+template <typename R>
+cudaError_t launch_bicg_sol(double2 *x64, long long xinst, const typename Cx<R>::T *V, long long vinst,
+                            const BicgPtrs &bp, const int *need, cudaStream_t st);
+cudaError_t launch_bicg_advance(const BicgPtrs &bp, cudaGraphConditionalHandle h, cudaStream_t st);
+
 // adjoint gradient (adjoint.cu)
 cudaError_t launch_adj_scatter(const Geo &g, const double2 *lam, const double2 *E, const Inst *inst, const double *iden,
                                double2 *grid, cudaStream_t st);

@@ -22,47 +22,11 @@
 // no waiting).
 #include "kernels.h"
 #include "reduce.cuh"
+#include "vec.cuh"
 
 namespace gsm {
 
-constexpr int KT = 256;  // threads per block of the vector kernels
 constexpr int MAXM = 128;
-
-// Vectors are stored with a stride Us (the length U rounded up to 64
-// complex values, pads held at zero), so each thread moves EPT consecutive
-// values with 16-byte loads: a tile is KT * EPT values.
-template <typename R> struct Ept { static constexpr int v = sizeof(R) == 4 ? 8 : 4; };
-
-template <typename C, int EPT> __device__ __forceinline__ void load_ept(C (&d)[EPT], const C *src) {
-  if constexpr (sizeof(C) == 8) {
-    const float4 *q = reinterpret_cast<const float4 *>(src);
-#pragma unroll
-    for (int k = 0; k < EPT / 2; ++k) {
-      const float4 t = q[k];
-      d[2 * k] = mk(t.x, t.y);
-      d[2 * k + 1] = mk(t.z, t.w);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) d[k] = src[k];
-  }
-}
-
-template <typename C, int EPT> __device__ __forceinline__ void store_ept(C *dst, const C (&d)[EPT]) {
-  if constexpr (sizeof(C) == 8) {
-    float4 *q = reinterpret_cast<float4 *>(dst);
-#pragma unroll
-    for (int k = 0; k < EPT / 2; ++k) q[k] = make_float4(d[2 * k].x, d[2 * k].y, d[2 * k + 1].x, d[2 * k + 1].y);
-  } else {
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) dst[k] = d[k];
-  }
-}
-
-template <typename R> __device__ __forceinline__ R warp_sum(R v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // h_i = <v_i, w> for i < nv and ||w||^2: w is held in registers per tile,
 // every basis vector streamed once.  Each block takes a group of GV basis
@@ -295,8 +259,8 @@ __global__ void __launch_bounds__(32 * FIN_W) k_finish(KrylovPtrs k, int j) {
 // block per instance: all threads stage the upper triangle (column l at
 // l (l + 1) / 2) in shared memory, then warp 0 substitutes column by
 // column, every lane updating its rows of the right-hand side.
-constexpr int BS_T = 256;
-__global__ void __launch_bounds__(BS_T) k_backsolve(KrylovPtrs k) {
+constexpr int BSOLVE_T = 256;
+__global__ void __launch_bounds__(BSOLVE_T) k_backsolve(KrylovPtrs k) {
   extern __shared__ __align__(16) unsigned char bs_dyn[];
   double2 *Rs = reinterpret_cast<double2 *>(bs_dyn);   // m (m + 1) / 2 entries
   __shared__ double2 s_s[MAXM];
@@ -509,7 +473,7 @@ cudaError_t launch_advance(const KrylovPtrs &k, cudaGraphConditionalHandle h, cu
 cudaError_t launch_backsolve(const KrylovPtrs &k, cudaStream_t st) {
   const size_t smem = sizeof(double2) * (size_t)k.m * (k.m + 1) / 2;
   cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_backsolve<<<k.B, BS_T, smem, st>>>(k);
+  k_backsolve<<<k.B, BSOLVE_T, smem, st>>>(k);
   return cudaGetLastError();
 }
 

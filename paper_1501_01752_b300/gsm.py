@@ -133,7 +133,7 @@ def plan_query(periods, n_harm, precision=FP32_REFINE, fft=(0, 0, 0), max_batch=
 
 
 def _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, max_batch, hbm_cap, device,
-          stream, fft, residual=RESID_AUTO):
+          stream, fft, residual=RESID_AUTO, krylov=GMRES):
     d = PlanDesc()
     for a in range(3):
         d.period[a] = periods[a]
@@ -142,7 +142,7 @@ def _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, 
     d.eps_b[0] = float(np.real(eps_b))
     d.eps_b[1] = float(np.imag(eps_b))
     d.precision = precision
-    d.krylov = GMRES
+    d.krylov = krylov
     d.restart = restart
     d.max_iter = max_iter
     d.tol = tol
@@ -159,13 +159,14 @@ class Plan:
     """One structure truncation on one GPU (gsm_plan_t)."""
 
     def __init__(self, periods, n_harm, eps_b=1.0, precision=FP32_REFINE, restart=0, max_iter=0, tol=0.0,
-                 inner_tol=0.0, max_batch=0, hbm_cap=0, device=0, stream=None, fft=(0, 0, 0), residual=RESID_AUTO):
+                 inner_tol=0.0, max_batch=0, hbm_cap=0, device=0, stream=None, fft=(0, 0, 0), residual=RESID_AUTO,
+                 krylov=GMRES):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
         self.n_harm = tuple(n_harm)
         self.desc = _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, max_batch,
-                          hbm_cap, device, stream, fft, residual)
+                          hbm_cap, device, stream, fft, residual, krylov)
         h = ct.c_void_p()
         s = lib.gsm_plan(ct.byref(self.desc), ct.byref(h))
         if s:
