@@ -17,7 +17,8 @@ Modules
 coefficients  Fourier images of the permittivity ("Calculation details";
               coefficient array of Eq. 4).
 operator      The truncated Eq. 4 operator A = I - G (Delta/eps_b *), the
-              Green tensor, the explicit Toeplitz matrix and the FFT form.
+              Green tensor, the explicit Toeplitz matrix and the FFT form;
+              the H-field operator of Eq. 5 in both forms.
 solvers       Dense LU, GMRES with modified Gram-Schmidt (Saad), BiCGSTAB.
 poles         Resonance model Eq. 6 and the pole fit of Eqs. 7-10.
 retrieval     Response xi(kappa), kappa sweeps and the effective tensor.

@@ -125,3 +125,15 @@ def delta_coefficients(eps_d, eps_b):
     c = tuple(s // 2 for s in out.shape)
     out[c] -= eps_b
     return out / eps_b
+
+
+def inverse_delta_coefficients(inv_eps_d, eps_b):
+    """[delta - eps_b/eps]_d with the sign of Eq. 5 folded into its use: this
+    returns (eps_b/eps - 1)_d = eps_b (1/eps)_d - delta_d0, the Toeplitz
+    generator of the H-field formulation.  inv_eps_d are the Fourier
+    coefficients of 1/eps(r), found analytically like those of eps
+    ("Calculation details": no numerical inversion of the eps matrix)."""
+    out = eps_b * np.array(inv_eps_d, dtype=complex, copy=True)
+    c = tuple(s // 2 for s in out.shape)
+    out[c] -= 1.0
+    return out

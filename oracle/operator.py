@@ -156,3 +156,78 @@ class Operator:
         if self.mode == "direct":
             return v - toeplitz_apply_direct(DeltaH, w, self.n_harm)
         return v - toeplitz_apply_fft(DeltaH, w, self.n_harm)
+
+
+# --------------------------------------------------------------- Eq. 5
+# The H-field formulation (GSM section, Eq. 5):
+#
+#   H_m = H^inc_m + k_m x [ sum_m' (delta_{mm'} - (eps_b/eps)_{m-m'}) (k_m' x H_m') ] / (k_b^2 - k_m^2),
+#
+# i.e. with Delta'_d = (eps_b/eps - 1)_d the system A_H H = H^inc,
+#
+#   (A_H H)_m = H_m - k_m x (Delta' * (k x H))_m / (k_m^2 - k_b^2),
+#
+# where * is the Toeplitz (truncated convolution) product of every Cartesian
+# component.  Re-derived from curl (eps^-1 curl H) = k0^2 H: for a mode
+# exp(i k.r) with k.H = 0, curl curl -> k^2, so
+# (k_m^2 - k_b^2) H_m = k_m x sum_m' (eps_b/eps - 1)_{m-m'} (k_m' x H_m').
+
+def wavevector_field(n_harm, kinc, periods):
+    """k_m for every harmonic, shape (N_z, N_y, N_x, 3)."""
+    kx, ky, kz = wavevectors(n_harm, kinc, periods)
+    KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
+    return np.stack([KX, KY, KZ], axis=-1)
+
+
+def cross_apply(k, v):
+    """(k x v)_m for v of shape (3, N_z, N_y, N_x) and k of shape (N_z, N_y, N_x, 3)."""
+    kk = np.moveaxis(k, -1, 0)
+    return np.cross(kk, v, axis=0)
+
+
+def dense_operator_h(Delta_h, n_harm, kinc, periods, kb2):
+    """The explicit 3N x 3N matrix of Eq. 5, ordering [c][m_z][m_y][m_x]:
+    A_H = I - diag(1/(k^2 - k_b^2)) C T C with C = per-harmonic k x, T the
+    Toeplitz matrix of Delta' applied to each component."""
+    T = toeplitz_matrix(Delta_h, n_harm)
+    k = wavevector_field(n_harm, kinc, periods).reshape(-1, 3)
+    Nh = T.shape[0]
+    den = (k * k).sum(-1) - kb2
+    if np.any(np.abs(den) <= 1e-12 * max(abs(kb2), 1.0)):
+        raise ZeroDivisionError("k_m^2 = k_b^2 for some harmonic")
+    # cross-product matrix [k x] per harmonic: (k x v)_a = eps_abc k_b v_c
+    Cx = np.zeros((3 * Nh, 3 * Nh))
+    for a in range(3):
+        b, c = (a + 1) % 3, (a + 2) % 3
+        Cx[a * Nh:(a + 1) * Nh, c * Nh:(c + 1) * Nh] += np.diag(k[:, b])
+        Cx[a * Nh:(a + 1) * Nh, b * Nh:(b + 1) * Nh] -= np.diag(k[:, c])
+    TT = np.zeros((3 * Nh, 3 * Nh), complex)
+    for a in range(3):
+        TT[a * Nh:(a + 1) * Nh, a * Nh:(a + 1) * Nh] = T
+    Dinv = np.tile(1.0 / den, 3)
+    return np.eye(3 * Nh) - Dinv[:, None] * (Cx @ TT @ Cx)
+
+
+class OperatorH:
+    """y = A_H x for Eq. 5 with a fixed structure and incident point (the
+    Toeplitz products by FFT, or by the explicit matrix with mode "direct")."""
+
+    def __init__(self, Delta_h, n_harm, kinc, periods, kb2, mode="fft"):
+        self.Delta, self.n_harm = Delta_h, tuple(n_harm)
+        self.k = wavevector_field(n_harm, kinc, periods)
+        den = (self.k * self.k).sum(-1) - kb2
+        if np.any(np.abs(den) <= 1e-12 * max(abs(kb2), 1.0)):
+            raise ZeroDivisionError("k_m^2 = k_b^2 for some harmonic")
+        self.iden = 1.0 / den
+        self.mode = mode
+        self.shape = (3,) + tuple(n_harm[::-1])
+
+    def toeplitz(self, x):
+        if self.mode == "direct":
+            return toeplitz_apply_direct(self.Delta, x, self.n_harm)
+        return toeplitz_apply_fft(self.Delta, x, self.n_harm)
+
+    def __call__(self, x):
+        x = np.asarray(x, complex).reshape(self.shape)
+        u = cross_apply(self.k, self.toeplitz(cross_apply(self.k, x)))
+        return x - self.iden[None] * u
