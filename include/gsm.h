@@ -63,6 +63,10 @@ enum { GSM_DF64 = 2 };
  * FP32 pipes where the lane-team product applies (FFT sizes 32/64), FP64
  * otherwise (AUTO), or FP64 always */
 enum { GSM_RESID_AUTO = 0, GSM_RESID_FP64 = 1 };
+/* the field the plan solves for: E of Eq. 4, or H of Eq. 5 (the H-field
+ * formulation, with the Fourier coefficients of 1/eps; point pol is then the
+ * incident H amplitude and the output field is H) */
+enum { GSM_FORM_E = 0, GSM_FORM_H = 1 };
 enum { GSM_GMRES = 0, GSM_BICGSTAB = 1 };            /* Krylov method            */
 enum { GSM_SPHERE = 0, GSM_BOX = 1, GSM_ELLIPSOID = 2 };
 
@@ -87,6 +91,7 @@ typedef struct {
   int device;           /* CUDA device ordinal                                           */
   void *cuda_stream;    /* cudaStream_t to issue work on; NULL = default stream          */
   int residual;         /* GSM_RESID_AUTO or GSM_RESID_FP64 (refined solves)             */
+  int form;             /* GSM_FORM_E (Eq. 4) or GSM_FORM_H (Eq. 5)                      */
 } gsm_plan_desc;
 
 /* Non-overlapping inclusion in the host medium (GSM section: analytic Fourier

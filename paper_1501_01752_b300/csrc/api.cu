@@ -147,6 +147,7 @@ static std::string check_desc(const gsm_plan_desc *d, int L[3]) {
   if (d->precision != GSM_FP64 && d->precision != GSM_FP32_REFINE) return "precision must be GSM_FP64 or GSM_FP32_REFINE";
   if (d->krylov != GSM_GMRES && d->krylov != GSM_BICGSTAB) return "krylov must be GSM_GMRES or GSM_BICGSTAB";
   if (d->residual != GSM_RESID_AUTO && d->residual != GSM_RESID_FP64) return "residual must be GSM_RESID_AUTO or GSM_RESID_FP64";
+  if (d->form != GSM_FORM_E && d->form != GSM_FORM_H) return "form must be GSM_FORM_E or GSM_FORM_H";
   if (d->restart < 0 || d->restart > 120) return "restart must be in [0, 120]";
   if (d->max_batch < 0 || d->max_batch > 4096) return "max_batch must be in [0, 4096]";
   return "";
@@ -311,11 +312,33 @@ static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
   const Geo &g = lv.g;
   const int D[3] = {2 * g.n[0], 2 * g.n[1], 2 * g.n[2]};
   std::vector<cd> eps;
-  if (!p->vox.empty()) voxel_coefficients(p->vox.data(), p->M, D, eps);
-  else shapes_coefficients(p->eps_host, p->shapes.data(), (int)p->shapes.size(), p->d.period, D, eps);
   const double eb = p->d.eps_b[0];
   const int W0 = 2 * D[0] + 1, W1 = 2 * D[1] + 1, W2 = 2 * D[2] + 1;
-  eps[((size_t)D[2] * W1 + D[1]) * W0 + D[0]] -= eb;  // Delta eps = eps - eps_b at d = 0
+  const size_t c0 = ((size_t)D[2] * W1 + D[1]) * W0 + D[0];
+  if (p->d.form == GSM_FORM_H) {
+    // Eq. 5: the coefficients of 1/eps, analytic like those of eps
+    // ("Calculation details"), then (eps_b/eps - 1)_d = eps_b (1/eps)_d - delta_d0;
+    // the generic scaling below divides by eps_b, so eps_b^2 (1/eps)_d - eps_b is stored
+    if (!p->vox.empty()) {
+      std::vector<double> inv(p->vox.size());
+      for (size_t i = 0; i < inv.size(); ++i) inv[i] = 1.0 / p->vox[i];
+      voxel_coefficients(inv.data(), p->M, D, eps);
+    } else {
+      std::vector<gsm_shape> inv(p->shapes);
+      for (auto &sh : inv) {
+        const cd e = 1.0 / cd(sh.eps[0], sh.eps[1]);
+        sh.eps[0] = e.real();
+        sh.eps[1] = e.imag();
+      }
+      shapes_coefficients(1.0 / p->eps_host, inv.data(), (int)inv.size(), p->d.period, D, eps);
+    }
+    for (auto &v : eps) v *= eb * eb;
+    eps[c0] -= eb;
+  } else {
+    if (!p->vox.empty()) voxel_coefficients(p->vox.data(), p->M, D, eps);
+    else shapes_coefficients(p->eps_host, p->shapes.data(), (int)p->shapes.size(), p->d.period, D, eps);
+    eps[c0] -= eb;  // Delta eps = eps - eps_b at d = 0
+  }
   const size_t LL = (size_t)g.L[0] * g.L[1] * g.L[2];
   std::vector<double2> grid(LL, make_double2(0.0, 0.0));
   for (int dz = -D[2]; dz <= D[2]; ++dz)
@@ -735,6 +758,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   mv.ystride = vinst;
   mv.write_back = 1;
   mv.mode = adj ? 2 : 0;
+  mv.form = p->d.form;
   mv.scale = sizeof(R) == 4 ? (const R *)k.scale32 : (const R *)k.scale64;
   MatvecArgs<double> rs;  // FP64 residual b - A x
   rs.g = g;
@@ -750,6 +774,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   rs.iden = w->iden64;
   rs.tw = p->tw64;
   rs.mode = adj ? 3 : 1;
+  rs.form = p->d.form;
   rs.partial = w->mv_partial;
   rs.counter = w->mv_counter;
   rs.norm_out = w->mv_norm;
@@ -771,6 +796,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   rd.iden = w->idendf;
   rd.tw = p->twdf;
   rd.mode = 1;
+  rd.form = p->d.form;
   rd.partial = w->mv_partial;
   rd.counter = w->mv_counter;
   rd.norm_out = w->mv_norm;
@@ -1130,6 +1156,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     return fail(p, GSM_ERR_ARG, "gsm_apply: unknown precision");
   if (precision == GSM_DF64 && (adjoint || p->team_only || !reg_path_ok(g) || !lv->Ddf))
     return fail(p, GSM_ERR_ARG, "gsm_apply: the double-float product needs FFT sizes 32/64 and adjoint = 0");
+  if (adjoint && p->d.form != GSM_FORM_E) return fail(p, GSM_ERR_ARG, "gsm_apply: the adjoint exists for the E-field form");
   const int prec = precision == GSM_FP32_REFINE;
   Work *w;
   if ((s = get_work(p, g, n, 2, 0, &w))) return s;
@@ -1161,6 +1188,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.iden = w->iden32;
     a.tw = p->tw32;
     a.mode = adjoint ? 2 : 0;
+    a.form = p->d.form;
     CK(matvec<float>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
     CK(launch_convert_f2d(yf, yd, (long long)n * g.U, st));
   } else if (precision == GSM_DF64) {
@@ -1177,6 +1205,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.iden = w->idendf;
     a.tw = p->twdf;
     a.mode = 0;
+    a.form = p->d.form;
     CK(matvec<dfl>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
   } else {
     MatvecArgs<double> a;
@@ -1192,6 +1221,7 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.iden = w->iden64;
     a.tw = p->tw64;
     a.mode = adjoint ? 2 : 0;
+    a.form = p->d.form;
     CK(matvec<double>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
   }
   CK(cudaMemcpyAsync(y, yd, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
@@ -1284,9 +1314,14 @@ gsm_status gsm_fit_poles(int n, const double *kappa, const double *xi, int Np, i
 // principal sweeps: (kdir, a) = (z, x), (z, y), (x, z)
 static const double PR_K[3][3] = {{0, 0, 1}, {0, 0, 1}, {1, 0, 0}};
 static const double PR_A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+// the same modes by their H polarisation (Eq. 5): H along k x E
+static const double PR_AH[3][3] = {{0, 1, 0}, {1, 0, 0}, {0, 1, 0}};
 
-static void principal_points(double k0, const double lohi[6], int nk, std::vector<gsm_point> &pts,
-                             std::vector<double> &kap) {
+static const double (*principal_pol(const gsm_plan_t *p))[3] { return p->d.form == GSM_FORM_H ? PR_AH : PR_A; }
+
+static void principal_points(const gsm_plan_t *p, double k0, const double lohi[6], int nk,
+                             std::vector<gsm_point> &pts, std::vector<double> &kap) {
+  const double(*PA)[3] = principal_pol(p);
   pts.clear();
   kap.clear();
   for (int c = 0; c < 3; ++c)
@@ -1296,7 +1331,7 @@ static void principal_points(double k0, const double lohi[6], int nk, std::vecto
       pt.k0 = k0;
       for (int a = 0; a < 3; ++a) {
         pt.kdir[a] = PR_K[c][a];
-        pt.pol[2 * a] = PR_A[c][a];
+        pt.pol[2 * a] = PA[c][a];
       }
       pt.kappa = kv;
       pts.push_back(pt);
@@ -1311,7 +1346,7 @@ extern "C" gsm_status gsm_retrieve_tensor(gsm_plan_t *p, double k0, const double
     return fail(p, GSM_ERR_ARG, "bad retrieval arguments (need n_kappa >= Nd + Np, Nd > Np)");
   std::vector<gsm_point> pts;
   std::vector<double> kap;
-  principal_points(k0, kappa_lo_hi, n_kappa, pts, kap);
+  principal_points(p, k0, kappa_lo_hi, n_kappa, pts, kap);
   std::vector<double> e0(6 * pts.size());
   gsm_status s = gsm_sweep(p, (int)pts.size(), pts.data(), e0.data(), nullptr);
   if (s) return s;
@@ -1320,7 +1355,7 @@ extern "C" gsm_status gsm_retrieve_tensor(gsm_plan_t *p, double k0, const double
     for (int i = 0; i < n_kappa; ++i) {
       const int q = c * n_kappa + i;
       cd v = 0;
-      for (int a = 0; a < 3; ++a) v += PR_A[c][a] * cd(e0[6 * q + 2 * a], e0[6 * q + 2 * a + 1]);  // a^H E_0
+      for (int a = 0; a < 3; ++a) v += principal_pol(p)[c][a] * cd(e0[6 * q + 2 * a], e0[6 * q + 2 * a + 1]);  // a^H E_0
       xi[i] = v;
     }
     if (fit_poles(n_kappa, &kap[c * n_kappa], xi.data(), Np, Nd, eta.data(), zeta.data()))
@@ -1378,6 +1413,7 @@ static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0 && v <= TWN_HOST; }
 // point): forward and adjoint solves per batch, correlation on the L grid,
 // fold onto the voxel grid, one voxel FFT.  grad (host) is accumulated.
 static gsm_status adjoint_impl(gsm_plan_t *p, int n, const gsm_point *points, const double *gE0, double *grad) {
+  if (p->d.form != GSM_FORM_E) return fail(p, GSM_ERR_ARG, "the adjoint gradient is built for the E-field form (Eq. 4)");
   if (p->vox.empty()) return fail(p, GSM_ERR_STATE, "gsm_adjoint needs a voxel permittivity");
   if (!pow2(p->M[0]) || !pow2(p->M[1]) || !pow2(p->M[2]))
     return fail(p, GSM_ERR_ARG, "gsm_adjoint needs power-of-two voxel grid sizes (<= 256)");
@@ -1463,10 +1499,11 @@ extern "C" gsm_status gsm_retrieve_tensor_grad(gsm_plan_t *p, double k0, const d
   if (!p) return GSM_ERR_ARG;
   if (!kappa_lo_hi || !eps_eff || !weights || !grad_voxel || n_kappa < Nd + Np || Nd <= Np || Np < 1 || !(k0 > 0))
     return fail(p, GSM_ERR_ARG, "bad retrieval arguments (need n_kappa >= Nd + Np, Nd > Np)");
+  if (p->d.form != GSM_FORM_E) return fail(p, GSM_ERR_ARG, "the adjoint gradient is built for the E-field form (Eq. 4)");
   cudaSetDevice(p->d.device);
   std::vector<gsm_point> pts;
   std::vector<double> kap;
-  principal_points(k0, kappa_lo_hi, n_kappa, pts, kap);
+  principal_points(p, k0, kappa_lo_hi, n_kappa, pts, kap);
   std::vector<double> e0(6 * pts.size());
   gsm_status s = gsm_sweep(p, (int)pts.size(), pts.data(), e0.data(), nullptr);
   if (s) return s;
@@ -1516,6 +1553,7 @@ gsm_status plan_full_level(gsm_plan_t *p, PlanView *v) {
   auto it = p->levels.find(key);
   if (it == p->levels.end() || !it->second.D64) return fail(p, GSM_ERR_STATE, "the plan's truncation level is not built");
   v->g = it->second.g;
+  v->form = p->d.form;
   v->D64 = it->second.D64;
   v->tw64 = p->tw64;
   v->st = p->st;

@@ -87,6 +87,7 @@ template <typename R> struct MatvecArgs {
   const R *iden = nullptr; // [B][Nh] 1/(k_m^2 - k_b^2)
   const C *tw = nullptr;   // 256-entry twiddle table
   int mode = 0;            // 0: A x, 1: b - A x, 2: A^H x, 3: b - A^H x
+  int form = 0;            // 0: Eq. 4 (E field), 1: Eq. 5 (H field; modes 0 and 1 only)
   double *partial = nullptr;
   unsigned *counter = nullptr;
   double *norm_out = nullptr;  // ||Y||^2 per instance (nullptr = skip)
@@ -202,6 +203,7 @@ cudaError_t launch_adj_real(const double2 *Q, long long n, double scale, double 
 // read-only view of a plan for entry points outside api.cu
 struct PlanView {
   Geo g;
+  int form;                // 0: Eq. 4, 1: Eq. 5 (the operator D64 belongs to)
   const double *D64;
   const double2 *tw64;
   cudaStream_t st;

@@ -27,7 +27,9 @@ namespace gsm {
 template <typename C> __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
 
 // ---------------------------------------------------------------- pass 1
-template <typename R, bool ADJ>
+// PRE 0: the input as it is (Eq. 4); PRE 1: G(m) x first (adjoint of Eq. 4);
+// PRE 2: k_m x x first (Eq. 5, H-field formulation)
+template <typename R, int PRE>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
                         typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale, int write_back,
                         const int *__restrict__ act, const Inst *__restrict__ inst,
@@ -50,9 +52,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
   const long long Nh = g.Nh;
   Team tm(g.lg[0]);
   // Green tensor ingredients for the adjoint form (G applied before the
-  // Toeplitz product; G is real symmetric for real k and k_b^2)
+  // Toeplitz product; G is real symmetric for real k and k_b^2) and the wave
+  // vector of the H-field form
   R kb2 = 0, kz = 0;
-  if (ADJ) {
+  if (PRE) {
     kb2 = (R)inst[b].kb2;
     kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
   }
@@ -63,18 +66,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
       const int row = e / N0, mx = e - row * N0;
       const long long h = ((long long)mz * N1 + my0 + row) * N0 + mx;
       C v;
-      if (!ADJ) {
+      if (PRE == 0) {
         v = cscale(Xb[c * Nh + h], s);
         if (write_back) Xb[c * Nh + h] = v;
       } else {
         const R kx = (R)(inst[b].kinc[0] + (mx - g.n[0]) * g.K[0]);
         const R ky = (R)(inst[b].kinc[1] + (my0 + row - g.n[1]) * g.K[1]);
         const C v0 = cscale(Xb[h], s), v1 = cscale(Xb[Nh + h], s), v2 = cscale(Xb[2 * Nh + h], s);
-        const C kv = mk(kx * v0.x + ky * v1.x + kz * v2.x, kx * v0.y + ky * v1.y + kz * v2.y);
-        const R kc = c == 0 ? kx : (c == 1 ? ky : kz);
-        const C vc = c == 0 ? v0 : (c == 1 ? v1 : v2);
-        const R id = iden[b * Nh + h];
-        v = mk(id * (kb2 * vc.x - kc * kv.x), id * (kb2 * vc.y - kc * kv.y));
+        if (PRE == 1) {
+          const C kv = mk(kx * v0.x + ky * v1.x + kz * v2.x, kx * v0.y + ky * v1.y + kz * v2.y);
+          const R kc = c == 0 ? kx : (c == 1 ? ky : kz);
+          const C vc = c == 0 ? v0 : (c == 1 ? v1 : v2);
+          const R id = iden[b * Nh + h];
+          v = mk(id * (kb2 * vc.x - kc * kv.x), id * (kb2 * vc.y - kc * kv.y));
+        } else {
+          // (k x v)_c
+          if (c == 0) v = csub(cscale(v2, ky), cscale(v1, kz));
+          else if (c == 1) v = csub(cscale(v0, kz), cscale(v2, kx));
+          else v = csub(cscale(v1, kx), cscale(v0, ky));
+        }
       }
       S[row * P0 + wrap(mx, g.n[0], L0)] = v;
     }
@@ -87,7 +97,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
     }
     __syncthreads();
   }
-  if (ADJ && write_back) {
+  if (PRE && write_back) {
     for (int e = threadIdx.x; e < nr * N0; e += blockDim.x) {
       const int row = e / N0, mx = e - row * N0;
       const long long h = ((long long)mz * N1 + my0 + row) * N0 + mx;
@@ -150,7 +160,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_yz(Geo g, typen
 // MODE 1: Y = b - (X - G u)    (residual of Eq. 4; b = a at m = 0)
 // MODE 2: Y = X - u            (adjoint operator: G was applied in pass 1)
 // MODE 3: Y = b - (X - u)      (residual of the adjoint system)
-template <typename R, int MODE>
+// HF = 1 (modes 0, 1): Eq. 5, G u replaced by k_m x u / (k_m^2 - k_b^2)
+template <typename R, int MODE, int HF>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, const typename Cx<R>::T *__restrict__ T, const typename Cx<R>::T *__restrict__ X,
                         long long xstride, typename Cx<R>::T *__restrict__ Y, long long ystride,
                         const int *__restrict__ act, const Inst *__restrict__ inst, const R *__restrict__ iden,
@@ -200,7 +211,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
     const long long h = ((long long)mz * N1 + my0 + row) * N0 + mx;
     const int px = wrap(mx, g.n[0], L0);
     C u0 = S[(0 * rows + row) * P0 + px], u1 = S[(1 * rows + row) * P0 + px], u2 = S[(2 * rows + row) * P0 + px];
-    if (!(MODE & 2)) {
+    if (HF) {
+      const R kx = kxs[mx], ky = kys[row], id = iden[b * Nh + h];
+      const C w0 = csub(cscale(u2, ky), cscale(u1, kz)), w1 = csub(cscale(u0, kz), cscale(u2, kx)),
+              w2 = csub(cscale(u1, kx), cscale(u0, ky));
+      u0 = cscale(w0, id);
+      u1 = cscale(w1, id);
+      u2 = cscale(w2, id);
+    } else if (!(MODE & 2)) {
       const R kx = kxs[mx], ky = kys[row], id = iden[b * Nh + h];
       const C ku = mk(kx * u0.x + ky * u1.x + kz * u2.x, kx * u0.y + ky * u1.y + kz * u2.y);
       u0 = mk(id * (kb2 * u0.x - kx * ku.x), id * (kb2 * u0.y - kx * ku.y));
@@ -295,15 +313,14 @@ cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *pro
     const size_t smem = cs * (TWN + (size_t)rows * (g.L[0] + 1));
     dim3 grid(g.N[2] * nchunk, a.B);
     if (prof) prof->begin(KIND_FWD_X, st);
-    if (a.mode & 2) {
-      cudaFuncSetAttribute(k_fwd_x<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fwd_x<R, true><<<grid, threads, smem, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
-                                                  a.iden, a.tw, rows, nchunk, a.jdev, a.jstride);
-    } else {
-      cudaFuncSetAttribute(k_fwd_x<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fwd_x<R, false><<<grid, threads, smem, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
-                                                   a.iden, a.tw, rows, nchunk, a.jdev, a.jstride);
-    }
+#define GSM_P1(PRE)                                                                                       \
+  cudaFuncSetAttribute(k_fwd_x<R, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
+  k_fwd_x<R, PRE><<<grid, threads, smem, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst, \
+                                               a.iden, a.tw, rows, nchunk, a.jdev, a.jstride)
+    if (a.mode & 2) { GSM_P1(1); }
+    else if (a.form) { GSM_P1(2); }
+    else { GSM_P1(0); }
+#undef GSM_P1
     if (prof) prof->end(KIND_FWD_X, st, (double)a.B * (cs * (double)(g.U + g.Tsz)));
   }
   // pass 2
@@ -326,14 +343,15 @@ cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *pro
     const size_t smem = cs * (TWN + 3 * (size_t)rows * (g.L[0] + 1)) + sizeof(R) * (g.N[0] + rows) + 16;
     dim3 grid(g.N[2] * nchunk, a.B);
     if (prof) prof->begin(KIND_INV_X, st);
-#define GSM_P3(M)                                                                                               \
-  cudaFuncSetAttribute(k_inv_x<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
-  k_inv_x<R, M><<<grid, threads, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, a.tw, \
-                                             rows, nchunk, a.partial, a.counter, a.norm_out, a.jdev, a.jstride)
-    if (a.mode == 0) { GSM_P3(0); }
-    else if (a.mode == 1) { GSM_P3(1); }
-    else if (a.mode == 2) { GSM_P3(2); }
-    else { GSM_P3(3); }
+#define GSM_P3(M, HF)                                                                                           \
+  cudaFuncSetAttribute(k_inv_x<R, M, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
+  k_inv_x<R, M, HF><<<grid, threads, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, \
+                                                 a.tw, rows, nchunk, a.partial, a.counter, a.norm_out, a.jdev,  \
+                                                 a.jstride)
+    if (a.mode == 0) { if (a.form) { GSM_P3(0, 1); } else { GSM_P3(0, 0); } }
+    else if (a.mode == 1) { if (a.form) { GSM_P3(1, 1); } else { GSM_P3(1, 0); } }
+    else if (a.mode == 2) { GSM_P3(2, 0); }
+    else { GSM_P3(3, 0); }
 #undef GSM_P3
     if (prof)
       prof->end(KIND_INV_X, st,

@@ -13,10 +13,13 @@
 //                        row (y inverse)
 //   pass 3  k_inv_x_t8 : team per (c, row): L_x -> N_x, then per harmonic
 //                        the Green tensor and y = x - G u (or the residual)
+#pragma once
 #include "fft_team8.cuh"
 #include "fft_team8x2.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
+
+#include <type_traits>
 
 namespace gsm {
 
@@ -104,6 +107,74 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
       const int rx = F::freq(ln.lane, q);
       Tb[((long long)rx * 3 + c) * N2 * N1] = v[i][q];
     }
+  }
+}
+
+// Pass 1 of the H-field form (Eq. 5): the x transforms of (k_m x x), one
+// team per (m_z, m_y) row holding all three components of the row, so that
+// the scaled write-back of a Krylov vector and the cross product read and
+// write only the team's own values.
+template <typename R, int L0, int TT>
+__global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__restrict__ X, long long xstride,
+                                                  typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
+                                                  int write_back, const int *__restrict__ act,
+                                                  const Inst *__restrict__ inst,
+                                                  const typename Cx<R>::T *__restrict__ twg, const int *__restrict__ jdev,
+                                                  long long jstride) {
+  using C = typename Cx<R>::T;
+  using IO = typename Io<R>::T;
+  using F = Team8<L0>;
+  if (jdev) X += (long long)(*jdev) * jstride;
+  constexpr int TS = F::TS, RB = TT / TS;
+  __shared__ C bufs[RB * F::BUF];
+  const int b = blockIdx.y;
+  if (act && !act[b]) return;
+  const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
+  const long long Nh = g.Nh;
+  const Lanes ln(TS);
+  C w[8];
+  F::twiddles(w, ln.lane, twg);
+  const long long nrows = (long long)N2 * N1;
+  const long long r = (long long)blockIdx.x * RB + ln.team;
+  const bool valid = r < nrows;
+  const R s = scale ? scale[b] : (R)1;
+  const int mz = (int)(r / N1), my = (int)(r - (long long)mz * N1);
+  const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
+  const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
+  IO *Xr = X + b * xstride + r * N0;
+  C v[3][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c][a] = mk((R)0, (R)0);
+    if (valid && h >= 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[c][a] = io_in<C>(Xr[c * Nh + h]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
+    const R kx = (R)(inst[b].kinc[0] + (h - g.n[0]) * g.K[0]);
+    C u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = mk(v[c][a].x * s, v[c][a].y * s);
+    if (write_back && valid && h >= 0)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Xr[c * Nh + h] = io_out<IO>(u[c]);
+    // (k x u), zero where no harmonic sits (u = 0 there)
+    v[0][a] = csub(cscale(u[2], ky), cscale(u[1], kz));
+    v[1][a] = csub(cscale(u[0], kz), cscale(u[2], kx));
+    v[2][a] = csub(cscale(u[1], kx), cscale(u[0], ky));
+  }
+  C *Tb = T + b * g.Tsz + (long long)mz * N1 + my;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    F::template forward<+1>(v[c], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
+    if (valid)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) Tb[((long long)F::freq(ln.lane, q) * 3 + c) * N2 * N1] = v[c][q];
   }
 }
 
@@ -322,25 +393,11 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, c
   }
 }
 
-// Dp[r_x / 2][r_y][r_z] = (D[r_x][r_y][r_z], D[r_x + 1][r_y][r_z])
-__global__ void k_pair_d(const float *__restrict__ D, float2 *__restrict__ Dp, long long plane, long long npairs) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs * plane;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long xp = i / plane, e = i - xp * plane;
-    Dp[i] = make_float2(D[(2 * xp) * plane + e], D[(2 * xp + 1) * plane + e]);
-  }
-}
 
-cudaError_t launch_pair_d(const float *D, float2 *Dp, const Geo &g, cudaStream_t st) {
-  const long long plane = (long long)g.L[1] * g.L[2], npairs = g.L[0] / 2;
-  k_pair_d<<<148 * 4, 256, 0, st>>>(D, Dp, plane, npairs);
-  return cudaGetLastError();
-}
 
-bool packed_yz_ok(const Geo &g) { return g.L[1] == 64 && g.L[2] == 64 && g.L[0] % 2 == 0; }
-
-// MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u)
-template <typename R, int L0, int MODE, int TT>
+// MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u); HF = 1 (Eq. 5): G u is
+// replaced by k_m x u / (k_m^2 - k_b^2)
+template <typename R, int L0, int MODE, int TT, int HF>
 __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T *__restrict__ T,
                                                  const typename Io<R>::T *__restrict__ X, long long xstride,
                                                  typename Io<R>::T *__restrict__ Y, long long ystride,
@@ -431,13 +488,19 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     const C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
             u2 = S3[(2 * rows + row) * P + mx];
     const R kx = kxs[mx], ky = kys[row], kz = kzs[row];
-    const R kux = kx * u0.x + ky * u1.x + kz * u2.x, kuy = kx * u0.y + ky * u1.y + kz * u2.y;
-    y0.x -= id * (kb2 * u0.x - kx * kux);
-    y0.y -= id * (kb2 * u0.y - kx * kuy);
-    y1.x -= id * (kb2 * u1.x - ky * kux);
-    y1.y -= id * (kb2 * u1.y - ky * kuy);
-    y2.x -= id * (kb2 * u2.x - kz * kux);
-    y2.y -= id * (kb2 * u2.y - kz * kuy);
+    if (HF) {
+      y0 = csub(y0, cscale(csub(cscale(u2, ky), cscale(u1, kz)), id));
+      y1 = csub(y1, cscale(csub(cscale(u0, kz), cscale(u2, kx)), id));
+      y2 = csub(y2, cscale(csub(cscale(u1, kx), cscale(u0, ky)), id));
+    } else {
+      const R kux = kx * u0.x + ky * u1.x + kz * u2.x, kuy = kx * u0.y + ky * u1.y + kz * u2.y;
+      y0.x -= id * (kb2 * u0.x - kx * kux);
+      y0.y -= id * (kb2 * u0.y - kx * kuy);
+      y1.x -= id * (kb2 * u1.x - ky * kux);
+      y1.y -= id * (kb2 * u1.y - ky * kuy);
+      y2.x -= id * (kb2 * u2.x - kz * kux);
+      y2.y -= id * (kb2 * u2.y - kz * kuy);
+    }
     if (MODE == 1) {
       C a0 = mk((R)0, (R)0), a1 = a0, a2 = a0;
       if (h == h0) {
@@ -468,18 +531,9 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   if (norm_out) last_block_sum((double)acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
 }
 
-bool reg_path_ok(const Geo &g) {
-  auto ok = [](int L) { return L == 32 || L == 64; };
-  return ok(g.L[0]) && ok(g.L[1]) && ok(g.L[2]);
-}
 
 static int p3_rows(const Geo &g, int tb) { return (tb / (g.L[0] / 8)) / 3; }
 
-int matvec_reg_blocks_pass3(const Geo &g) {
-  if (!reg_path_ok(g)) return 1;
-  const int rows = p3_rows(g, 128);   // the smallest block the autotuner may pick
-  return (int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows);
-}
 
 constexpr int P1_RPT = 2;   // rows per team in pass 1
 
@@ -488,6 +542,17 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
   const Geo &g = a.g;
   const int RB = TT / (g.L[0] / 8) * P1_RPT;
   dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
+  if (a.form) {
+    const int RBH = TT / (g.L[0] / 8);
+    dim3 gridh((int)(((long long)g.N[2] * g.N[1] + RBH - 1) / RBH), a.B);
+    if (g.L[0] == 64)
+      k_fwd_x_t8h<R, 64, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
+                                                   a.tw, a.jdev, a.jstride);
+    else
+      k_fwd_x_t8h<R, 32, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
+                                                   a.tw, a.jdev, a.jstride);
+    return;
+  }
   if (g.L[0] == 64)
     k_fwd_x_t8<R, 64, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw,
                                                        a.jdev, a.jstride);
@@ -528,20 +593,27 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   const int rows = p3_rows(g, TT);
   const size_t smem = sizeof(C) * 3 * (size_t)rows * p3_pitch(g.N[0]) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
   dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);
-#define GSM_P3(L0, M)                                                                                          \
-  cudaFuncSetAttribute(k_inv_x_t8<R, L0, M, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
-  k_inv_x_t8<R, L0, M, TT><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, \
-                                                   a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, a.jstride)
+#define GSM_P3(L0, M, HF)                                                                                         \
+  cudaFuncSetAttribute(k_inv_x_t8<R, L0, M, TT, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+  k_inv_x_t8<R, L0, M, TT, HF><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,     \
+                                                       a.iden, a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, \
+                                                       a.jstride)
   if (g.L[0] == 64) {
-    if (a.mode == 1) { GSM_P3(64, 1); } else { GSM_P3(64, 0); }
+    if (a.form) { if (a.mode == 1) { GSM_P3(64, 1, 1); } else { GSM_P3(64, 0, 1); } }
+    else { if (a.mode == 1) { GSM_P3(64, 1, 0); } else { GSM_P3(64, 0, 0); } }
   } else {
-    if (a.mode == 1) { GSM_P3(32, 1); } else { GSM_P3(32, 0); }
+    if (a.form) { if (a.mode == 1) { GSM_P3(32, 1, 1); } else { GSM_P3(32, 0, 1); } }
+    else { if (a.mode == 1) { GSM_P3(32, 1, 0); } else { GSM_P3(32, 0, 0); } }
   }
 #undef GSM_P3
 }
 
 template <typename R, template <typename, int> class F>
 static cudaError_t dispatch_tb(int tb, const MatvecArgs<R> &a, cudaStream_t st) {
+  if constexpr (std::is_same<R, dfl>::value) {   // the double-float product runs with 256 threads only
+    F<R, 256>::run(a, st);
+    return cudaGetLastError();
+  }
   if (tb == 128) F<R, 128>::run(a, st);
   else if (tb == 512) F<R, 512>::run(a, st);
   else F<R, 256>::run(a, st);
@@ -577,11 +649,5 @@ cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler 
   if (prof) prof->end(KIND_INV_X, st, (double)a.B * (cs * (double)(g.Tsz + 2 * g.U) + sizeof(R) * (double)g.Nh));
   return cudaGetLastError();
 }
-
-template cudaError_t launch_matvec_reg<float>(const MatvecArgs<float> &, cudaStream_t, Profiler *, const int *);
-template cudaError_t launch_matvec_reg<double>(const MatvecArgs<double> &, cudaStream_t, Profiler *, const int *);
-template cudaError_t launch_reg_pass<float>(int, int, const MatvecArgs<float> &, cudaStream_t);
-template cudaError_t launch_reg_pass<double>(int, int, const MatvecArgs<double> &, cudaStream_t);
-template cudaError_t launch_matvec_reg<dfl>(const MatvecArgs<dfl> &, cudaStream_t, Profiler *, const int *);
 
 }  // namespace gsm

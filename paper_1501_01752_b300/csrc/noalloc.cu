@@ -99,6 +99,7 @@ extern "C" gsm_status gsm_apply_noalloc(gsm_plan_t *p, const gsm_point *point, c
     a.iden = iden64;
     a.tw = v.tw64;
     a.mode = 0;
+    a.form = v.form;   // the plan's operator: Eq. 4, or Eq. 5 for an H-field plan
     e = launch_matvec<double>(a, v.st, nullptr);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(v.st);

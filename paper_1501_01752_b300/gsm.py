@@ -23,6 +23,7 @@ STATUS_NAMES = ["GSM_OK", "GSM_ERR_ARG", "GSM_ERR_SINGULAR", "GSM_ERR_NOCONV", "
 FP64, FP32_REFINE = 0, 1
 DF64 = 2                      # gsm_apply only: the double-float product (outer-residual arithmetic)
 RESID_AUTO, RESID_FP64 = 0, 1
+FORM_E, FORM_H = 0, 1         # Eq. 4 (E field) or Eq. 5 (H field)
 GMRES, BICGSTAB = 0, 1
 KIND_FWD_X, KIND_YZ, KIND_INV_X, KIND_DOTS, KIND_UPDATE, KIND_OTHER, KIND_RESID64, KIND_LAUNCHES = range(8)
 
@@ -38,7 +39,8 @@ class PlanDesc(ct.Structure):
                 ("eps_b", ct.c_double * 2), ("precision", ct.c_int), ("krylov", ct.c_int),
                 ("restart", ct.c_int), ("max_iter", ct.c_int), ("tol", ct.c_double),
                 ("inner_tol", ct.c_double), ("max_batch", ct.c_int), ("hbm_cap_bytes", ct.c_size_t),
-                ("device", ct.c_int), ("cuda_stream", ct.c_void_p), ("residual", ct.c_int)]
+                ("device", ct.c_int), ("cuda_stream", ct.c_void_p), ("residual", ct.c_int),
+                ("form", ct.c_int)]
 
 
 class Shape(ct.Structure):
@@ -133,7 +135,7 @@ def plan_query(periods, n_harm, precision=FP32_REFINE, fft=(0, 0, 0), max_batch=
 
 
 def _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, max_batch, hbm_cap, device,
-          stream, fft, residual=RESID_AUTO, krylov=GMRES):
+          stream, fft, residual=RESID_AUTO, krylov=GMRES, form=FORM_E):
     d = PlanDesc()
     for a in range(3):
         d.period[a] = periods[a]
@@ -152,6 +154,7 @@ def _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, 
     d.device = device
     d.cuda_stream = stream
     d.residual = residual
+    d.form = form
     return d
 
 
@@ -160,13 +163,13 @@ class Plan:
 
     def __init__(self, periods, n_harm, eps_b=1.0, precision=FP32_REFINE, restart=0, max_iter=0, tol=0.0,
                  inner_tol=0.0, max_batch=0, hbm_cap=0, device=0, stream=None, fft=(0, 0, 0), residual=RESID_AUTO,
-                 krylov=GMRES):
+                 krylov=GMRES, form=FORM_E):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
         self.n_harm = tuple(n_harm)
         self.desc = _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, max_batch,
-                          hbm_cap, device, stream, fft, residual, krylov)
+                          hbm_cap, device, stream, fft, residual, krylov, form)
         h = ct.c_void_p()
         s = lib.gsm_plan(ct.byref(self.desc), ct.byref(h))
         if s:
