@@ -180,6 +180,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="relative tolerance of the complex64 inner GMRES cycles (0 = library default 1e-4)")
+    ap.add_argument("--form", default="e", choices=["e", "h"],
+                    help="E-field (Eq. 4) or H-field (Eq. 5) formulation; points keep their polarisation as H amplitude")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"],
                     help="Krylov method of the refined solve (and of the FP64 plain path)")
     ap.add_argument("--residual", default="auto", choices=["auto", "fp64"],
@@ -211,6 +213,7 @@ def main():
         return gsm.plan_for(st, N_HARM, precision=prec, tol=TOL, max_batch=B, device=local,
                             stream=stream.cuda_stream, inner_tol=args.inner_tol,
                             krylov=gsm.BICGSTAB if args.krylov == "bicgstab" else gsm.GMRES,
+                            form=gsm.FORM_H if args.form == "h" else gsm.FORM_E,
                             residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO)
 
     plan = make_plan(gsm.FP32_REFINE)
@@ -287,6 +290,7 @@ def main():
     if args.alt_steps > 0:
         palt = gsm.plan_for(st, N_HARM, precision=gsm.FP32_REFINE, tol=TOL, max_batch=B, device=local,
                             stream=stream.cuda_stream, inner_tol=args.inner_tol,
+                            form=gsm.FORM_H if args.form == "h" else gsm.FORM_E,
                             krylov=gsm.BICGSTAB if alt == "bicgstab" else gsm.GMRES,
                             residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO)
         palt.solve(pts, out=E)
@@ -337,7 +341,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec + c128 refinement", "data": "synthetic",
         "config": {"workload": "woodpile eps 11.9 in eps_b 1, Lambda 0.35, 31^3 harmonics, 64^3 FFT grid",
-                   "global_batch": B * ws, "tol": TOL, "krylov": args.krylov,
+                   "global_batch": B * ws, "tol": TOL, "krylov": args.krylov, "form": args.form.upper(),
                    "l2": "flushed between steps (inputs+basis > L2)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "fp64_plain": None if fp64_value is None else

@@ -60,7 +60,9 @@ struct Work {
   unsigned *mv_counter = nullptr;
   int *jcount = nullptr;    // device Arnoldi step counter of the captured cycle
   KrylovPtrs k{};
-  struct Cycle { int B, m, adj, force, prec; cudaGraph_t graph; cudaGraphExec_t exec; };
+  // a captured cycle holds its kernels' arguments by value, among them the
+  // level's multiplier (D, Dp): it is reused only while those are unchanged
+  struct Cycle { int B, m, adj, force, prec; const void *D, *Dp; cudaGraph_t graph; cudaGraphExec_t exec; };
   std::vector<Cycle> cycles;
   void drop_graphs() {
     for (auto &c : cycles) {
@@ -499,7 +501,9 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
                                    const KrylovPtrs &k, typename Cx<R>::T *V, long long vinst, long long Us, int adj) {
   const int prec = sizeof(R) == 4;
   for (auto &c : w->cycles)
-    if (c.B == k.B && c.m == k.m && c.adj == adj && c.force == k.force_reorth && c.prec == prec) return c.exec;
+    if (c.B == k.B && c.m == k.m && c.adj == adj && c.force == k.force_reorth && c.prec == prec && c.D == mv.D &&
+        c.Dp == mv.Dp)
+      return c.exec;
   if (!p->cap_st && cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
@@ -544,7 +548,7 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
     if (graph) cudaGraphDestroy(graph);
     return nullptr;
   }
-  w->cycles.push_back({k.B, k.m, adj, k.force_reorth, prec, graph, exec});
+  w->cycles.push_back({k.B, k.m, adj, k.force_reorth, prec, mv.D, mv.Dp, graph, exec});
   return exec;
 }
 
@@ -599,7 +603,9 @@ static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const Mat
   if (p->use_graphs && !prof) {
     cudaGraphExec_t exec = nullptr;
     for (auto &c : w->cycles)
-      if (c.B == bp.B && c.m == BS_COUNT - 1 && c.adj == (int)adj && c.force == -1 && c.prec == prec) exec = c.exec;
+      if (c.B == bp.B && c.m == BS_COUNT - 1 && c.adj == (int)adj && c.force == -1 && c.prec == prec &&
+          c.D == mv.D && c.Dp == mv.Dp)
+        exec = c.exec;
     if (!exec) {
       if (!p->cap_st && cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -634,7 +640,7 @@ static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const Mat
           if (graph) cudaGraphDestroy(graph);
           exec = nullptr;
         } else {
-          w->cycles.push_back({bp.B, BS_COUNT - 1, (int)adj, -1, prec, graph, exec});
+          w->cycles.push_back({bp.B, BS_COUNT - 1, (int)adj, -1, prec, mv.D, mv.Dp, graph, exec});
         }
       }
     }
@@ -1132,6 +1138,8 @@ gsm_status gsm_set_permittivity(gsm_plan_t *p, const double eps_host[2], const g
     kv.second.D32 = nullptr;
     kv.second.D32p = nullptr;
   }
+  // captured cycles read the freed multipliers: rebuild them on next use
+  for (auto &kv : p->works) kv.second.drop_graphs();
   Level *lv;
   return get_level(p, p->d.n_harm, &lv);
 }

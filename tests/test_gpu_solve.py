@@ -178,3 +178,25 @@ def test_singular_harmonic_anywhere_in_the_box():
         E, infos, s = plan.solve([ok])
         assert s == 0 and infos[0]["rel_residual"] <= 1e-10, (m, infos)
     plan.close()
+
+
+@pytest.mark.parametrize("krylov", ["gmres", "bicgstab"])
+def test_new_permittivity_rebuilds_captured_cycles(krylov):
+    # captured inner cycles hold the multiplier's device address; after
+    # gsm_set_permittivity the same plan must solve the new structure exactly
+    # like a fresh plan (and never read the freed multiplier)
+    g = gsm()
+    n_harm = (15, 15, 15)
+    pts = wl.woodpile_batch(4)
+    kr = g.BICGSTAB if krylov == "bicgstab" else g.GMRES
+    a, b = wl.woodpile(), wl.sphere_lattice(period=0.35)
+    plan = g.plan_for(a, n_harm, precision=g.FP32_REFINE, tol=1e-8, krylov=kr)
+    plan.solve(pts)
+    for st in (b, a, b):
+        plan.set_structure(st)
+        E, infos, s = plan.solve(pts)
+        fresh = g.plan_for(st, n_harm, precision=g.FP32_REFINE, tol=1e-8, krylov=kr)
+        E2, _, s2 = fresh.solve(pts)
+        fresh.close()
+        assert s == 0 and s2 == 0 and rel(E, E2) < 1e-12, rel(E, E2)
+    plan.close()
