@@ -128,11 +128,20 @@ static int fft_size(int N) {
   return L;
 }
 
-static int ilog2(int L) {
-  int l = 0;
-  while ((1 << l) < L) ++l;
-  return l;
+// FFT sizes of the product: powers of two up to 256, and 3 * 2^p from 24 to
+// 192 (mixed radix: one radix-3 stage, shared-memory FFT path only)
+static bool fft_supported(int L) {
+  if (L >= 1 && L <= 256 && (L & (L - 1)) == 0) return true;
+  return L % 3 == 0 && L >= 24 && L <= 192 && ((L / 3) & (L / 3 - 1)) == 0;
 }
+
+// the smallest mixed-radix size >= 2N - 1 when it is below the power of two, else 0
+static int mixed_size(int N) {
+  for (int L = 24; L <= 192; L *= 2)
+    if (L >= 2 * N - 1) return L < fft_size(N) ? L : 0;
+  return 0;
+}
+
 
 static std::string check_desc(const gsm_plan_desc *d, int L[3]) {
   if (!d) return "desc is NULL";
@@ -140,8 +149,10 @@ static std::string check_desc(const gsm_plan_desc *d, int L[3]) {
     if (!(d->period[a] > 0)) return "period must be positive";
     if (d->n_harm[a] < 1 || d->n_harm[a] % 2 == 0) return "n_harm must be odd and >= 1";
     int Lmin = fft_size(d->n_harm[a]);
-    int Lv = d->fft[a] ? d->fft[a] : Lmin;
-    if (Lv < 2 * d->n_harm[a] - 1 || (Lv & (Lv - 1)) || Lv > TWN_HOST) return "fft size must be a power of two in [2N-1, 256]";
+    if (d->fft[a] < -1) return "fft size must be -1 (tuned), 0 (power of two) or a supported size";
+    int Lv = d->fft[a] > 0 ? d->fft[a] : Lmin;   // -1: tuned per level, power of two until then
+    if (Lv < 2 * d->n_harm[a] - 1 || !fft_supported(Lv))
+      return "fft size must be >= 2N-1: a power of two <= 256 or 3 * 2^p in [24, 192]";
     L[a] = Lv;
   }
   if (d->eps_b[1] != 0.0) return "complex eps_b is not supported (lossless basis only)";
@@ -162,7 +173,6 @@ static Geo make_geo(const gsm_plan_desc &d, const int N[3], const int Lplan[3]) 
     g.n[a] = (N[a] - 1) / 2;
     // a reduced truncation uses its own smallest grid unless the plan's is forced
     g.L[a] = (N[a] == d.n_harm[a]) ? Lplan[a] : fft_size(N[a]);
-    g.lg[a] = ilog2(g.L[a]);
     g.K[a] = 2.0 * M_PI / d.period[a];
   }
   g.Nh = (long long)N[0] * N[1] * N[2];
@@ -1415,7 +1425,7 @@ extern "C" gsm_status gsm_profile_get(gsm_plan_t *p, int kind, long long *launch
   return GSM_OK;
 }
 
-static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0 && v <= TWN_HOST; }
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0 && v <= 256; }
 
 // Adjoint gradient for n points with objective gradients gE0 (6 doubles per
 // point): forward and adjoint solves per batch, correlation on the L grid,

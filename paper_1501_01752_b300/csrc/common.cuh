@@ -47,8 +47,7 @@ struct Inst {
 struct Geo {
   int N[3];        // harmonics per axis (odd)
   int n[3];        // (N - 1) / 2
-  int L[3];        // FFT points per axis (power of two, >= 2N - 1)
-  int lg[3];       // log2 L
+  int L[3];        // FFT points per axis (2^p or 3 * 2^p, >= 2N - 1)
   double K[3];     // reciprocal vectors 2 pi / Lambda
   long long Nh;    // N0 N1 N2
   long long U;     // 3 Nh complex unknowns per instance

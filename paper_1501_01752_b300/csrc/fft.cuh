@@ -1,26 +1,30 @@
 // Shared-memory FFT building blocks for the pruned 3D convolution.
 //
-// A line of L = 2^p complex values in shared memory is transformed in place
-// by a team of ts = max(1, L/8) consecutive lanes of one warp (the team never
-// straddles a warp, so it synchronises with __syncwarp on its own mask).
-// The transform is a Stockham autosort decomposition: radix-8 stages while at
-// least three bits remain, then one radix-4 or radix-2 stage; every stage
-// reads R values per group into registers, synchronises, applies the
-// twiddles exp(S 2 pi i k r / (Ns R)), an R-point DFT, and writes the R
-// outputs to their natural-order positions.  Output is in natural order.
+// A line of L complex values in shared memory, L = 2^p or L = 3 * 2^p with
+// p >= 3 (mixed radix: 24, 48, 96, 192), is transformed in place by a team of
+// ts = max(1, L/8) lanes of one warp.  Teams never straddle a warp: a warp
+// holds floor(32 / ts) teams and its remaining lanes stay idle, so every team
+// synchronises with __syncwarp on its own mask.  The transform is a Stockham
+// autosort decomposition: radix-8 stages while the remaining length has a
+// factor 8, then one radix-4 or radix-2 stage, and a final radix-3 stage
+// when L has a factor 3; every stage reads R values per group into
+// registers, synchronises, applies the twiddles exp(S 2 pi i k r / (Ns R))
+// (k = g mod Ns, Ns the product of the radices already applied), an R-point
+// DFT, and writes the R outputs to their natural-order positions.  Output is
+// in natural order.
 //
 //   S = +1:  X[q] = sum_j x[j] exp(+2 pi i j q / L)   (harmonics -> grid)
 //   S = -1:  X[q] = sum_j x[j] exp(-2 pi i j q / L)   (grid -> harmonics)
 //
-// Twiddles come from a 256-entry table tw[j] = exp(+2 pi i j / 256) built on
-// the host in FP64 and staged in shared memory; S = -1 uses its conjugate.
+// Twiddles come from a 768-entry table tw[j] = exp(+2 pi i j / 768) built on
+// the host in FP64 (768 = 3 * 256 holds every root of unity of the supported
+// sizes); S = -1 uses its conjugate.
 #pragma once
 #include "common.cuh"
 
 namespace gsm {
 
-constexpr int TWN = 256;     // table resolution = largest supported L
-constexpr int LG_TWN = 8;
+constexpr int TWN = 768;     // table resolution: every supported L divides it
 
 template <int S, typename C> __device__ __forceinline__ C mul_si(C a) {  // a * (S i)
   return S > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
@@ -63,20 +67,34 @@ template <int S, typename C> __device__ __forceinline__ void dft8(C* v) {
   v[7] = csub(e3, t3);
 }
 
-template <int LR, int S, typename C> __device__ __forceinline__ void dft_r(C* v) {
-  if constexpr (LR == 3) dft8<S>(v);
-  else if constexpr (LR == 2) dft4<S>(v);
+// 3-point DFT: with w = exp(S 2 pi i / 3) = -1/2 + S i sqrt(3)/2,
+// X0 = v0 + v1 + v2, X1,2 = v0 - (v1 + v2)/2 +- S i (sqrt(3)/2) (v1 - v2)
+template <int S, typename C> __device__ __forceinline__ void dft3(C* v) {
+  using R = decltype(v[0].x);
+  const R h = (R)0.86602540378443864676;
+  const C t1 = cadd(v[1], v[2]);
+  const C t2 = mk(v[0].x - (R)0.5 * t1.x, v[0].y - (R)0.5 * t1.y);
+  const C d = csub(v[1], v[2]);
+  const C t3 = mul_si<S>(mk(h * d.x, h * d.y));
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(t2, t3);
+  v[2] = csub(t2, t3);
+}
+
+template <int R, int S, typename C> __device__ __forceinline__ void dft_r(C* v) {
+  if constexpr (R == 8) dft8<S>(v);
+  else if constexpr (R == 4) dft4<S>(v);
+  else if constexpr (R == 3) dft3<S>(v);
   else dft2<S>(v);
 }
 
-// One Stockham stage of radix R = 2^LR on a line of 2^lgL points; Ns = 2^lgNs
-// is the product of the radices already applied.
-template <int LR, int S, typename C>
-__device__ __forceinline__ void fft_stage(C* line, int lgL, int lgNs, int lane, int ts, unsigned mask,
-                                          const C* tw) {
-  constexpr int R = 1 << LR;
-  constexpr int MAXG = 8 / R;   // groups per lane: ts = max(1, L/8) => L/(R ts) <= 8/R
-  const int ngroups = 1 << (lgL - LR);
+// One Stockham stage of radix R on a line of L points; Ns is the product of
+// the radices already applied.  ts = max(1, L / 8) lanes share the L / R
+// groups, at most ceil(8 / R) per lane.
+template <int R, int S, typename C>
+__device__ __forceinline__ void fft_stage(C* line, int L, int Ns, int lane, int ts, unsigned mask, const C* tw) {
+  constexpr int MAXG = (8 + R - 1) / R;
+  const int ngroups = L / R;
   C v[MAXG][R];
 #pragma unroll
   for (int q = 0; q < MAXG; ++q) {
@@ -87,54 +105,71 @@ __device__ __forceinline__ void fft_stage(C* line, int lgL, int lgNs, int lane, 
     }
   }
   __syncwarp(mask);
-  const int Ns = 1 << lgNs;
-  const int sh = LG_TWN - lgNs - LR;
+  const int step = TWN / (Ns * R);   // table stride of exp(2 pi i / (Ns R))
 #pragma unroll
   for (int q = 0; q < MAXG; ++q) {
     int g = lane + q * ts;
     if (g < ngroups) {
-      const int k = g & (Ns - 1);
-      if (lgNs > 0) {
+      const int k = g % Ns;
+      if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          C w = tw[(k * r) << sh];
+          C w = tw[k * r * step];
           if (S < 0) w.y = -w.y;
           v[q][r] = cmul(v[q][r], w);
         }
       }
-      dft_r<LR, S>(v[q]);
-      const int base = ((g - k) << LR) + k;
+      dft_r<R, S>(v[q]);
+      const int base = (g - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) line[base + (r << lgNs)] = v[q][r];
+      for (int r = 0; r < R; ++r) line[base + r * Ns] = v[q][r];
     }
   }
   __syncwarp(mask);
 }
 
-// In-place FFT of one line of 2^lgL points by a team of ts lanes.
+// In-place FFT of one line of L points (2^p or 3 * 2^p) by a team of ts
+// lanes: radix-8 stages over the power-of-two part, one radix-4 or radix-2
+// stage for what remains of it, then a radix-3 stage when 3 divides L.
 template <int S, typename C>
-__device__ __forceinline__ void team_fft(C* line, int lgL, int lane, int ts, unsigned mask, const C* tw) {
-  int lgNs = 0, rem = lgL;
-  while (rem >= 3) {
-    fft_stage<3, S>(line, lgL, lgNs, lane, ts, mask, tw);
-    lgNs += 3;
-    rem -= 3;
+__device__ __forceinline__ void team_fft(C* line, int L, int lane, int ts, unsigned mask, const C* tw) {
+  const bool three = L % 3 == 0;
+  int rem = three ? L / 3 : L, Ns = 1;
+  while (rem >= 8) {
+    fft_stage<8, S>(line, L, Ns, lane, ts, mask, tw);
+    Ns *= 8;
+    rem /= 8;
   }
-  if (rem == 2) fft_stage<2, S>(line, lgL, lgNs, lane, ts, mask, tw);
-  else if (rem == 1) fft_stage<1, S>(line, lgL, lgNs, lane, ts, mask, tw);
+  if (rem == 4) {
+    fft_stage<4, S>(line, L, Ns, lane, ts, mask, tw);
+    Ns *= 4;
+  } else if (rem == 2) {
+    fft_stage<2, S>(line, L, Ns, lane, ts, mask, tw);
+    Ns *= 2;
+  }
+  if (three) fft_stage<3, S>(line, L, Ns, lane, ts, mask, tw);
 }
 
-// Team geometry for lines of 2^lgL points: team size, lane, team index, mask.
+// Team geometry for lines of L points: ts = max(1, L / 8) lanes per team,
+// floor(32 / ts) teams per warp (a team never straddles a warp).  When ts
+// does not divide 32 the last lanes of each warp are idle: their id is
+// IDLE (beyond any loop bound), so every "for (x = id; x < bound; x +=
+// count)" loop skips them and they never take part in a team's __syncwarp;
+// nothing may be computed from id outside such a loop.  blockDim.x is a
+// multiple of 32.
 struct Team {
+  static constexpr int IDLE = 1 << 30;
   int ts, lane, id, count;
   unsigned mask;
-  __device__ __forceinline__ Team(int lgL) {
-    ts = lgL >= 3 ? (1 << (lgL - 3)) : 1;
-    lane = threadIdx.x % ts;
-    id = threadIdx.x / ts;
-    count = blockDim.x / ts;
-    unsigned m = ts == 32 ? 0xffffffffu : ((1u << ts) - 1u);
-    mask = m << ((threadIdx.x & 31) - lane);
+  __device__ __forceinline__ Team(int L) {
+    ts = L >= 8 ? L / 8 : 1;
+    const int per = 32 / ts, wl = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = wl / ts;
+    count = (blockDim.x >> 5) * per;
+    lane = wl - t * ts;
+    id = t < per ? w * per + t : IDLE;
+    const unsigned m = ts == 32 ? 0xffffffffu : ((1u << ts) - 1u);
+    mask = t < per ? m << (wl - lane) : 0u;
   }
 };
 

@@ -8,13 +8,13 @@
 namespace gsm {
 
 template <int S>
-__global__ void __launch_bounds__(256) k_fft_axis(double2 *data, int Lx, int Ly, int Lz, int axis, int lg, long long bstride, int nl,
+__global__ void __launch_bounds__(256) k_fft_axis(double2 *data, int Lx, int Ly, int Lz, int axis, int Ln, long long bstride, int nl,
                            const double2 *__restrict__ twg) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   double2 *tw = reinterpret_cast<double2 *>(sm_raw);
   double2 *Sm = tw + TWN;
   load_twiddles(tw, twg);
-  const int L = 1 << lg, P = L + 1;
+  const int L = Ln, P = L + 1;
   const long long nlines = axis == 0 ? (long long)Ly * Lz : (axis == 1 ? (long long)Lz * Lx : (long long)Ly * Lx);
   const long long stride = axis == 0 ? 1 : (axis == 1 ? Lx : (long long)Lx * Ly);
   double2 *d = data + blockIdx.y * bstride;
@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(256) k_fft_axis(double2 *data, int Lx, int Ly,
     Sm[l * P + i] = d[base(l0 + l) + i * stride];
   }
   __syncthreads();
-  Team tm(lg);
-  for (int l = tm.id; l < cnt; l += tm.count) team_fft<S>(Sm + l * P, lg, tm.lane, tm.ts, tm.mask, tw);
+  Team tm(L);
+  for (int l = tm.id; l < cnt; l += tm.count) team_fft<S>(Sm + l * P, L, tm.lane, tm.ts, tm.mask, tw);
   __syncthreads();
   for (int e = threadIdx.x; e < cnt * L; e += blockDim.x) {
     int l, i;
@@ -48,8 +48,6 @@ cudaError_t launch_fft_axis(double2 *data, int Lx, int Ly, int Lz, int axis, int
                             long long batch_stride, const double2 *tw, cudaStream_t st) {
   const int L = axis == 0 ? Lx : (axis == 1 ? Ly : Lz);
   if (L == 1) return cudaSuccess;
-  int lg = 0;
-  while ((1 << lg) < L) ++lg;
   const long long nlines = axis == 0 ? (long long)Ly * Lz : (axis == 1 ? (long long)Lz * Lx : (long long)Ly * Lx);
   int nl = std::max(1, 4096 / L);
   const int ts = L >= 8 ? L / 8 : 1;
@@ -59,10 +57,10 @@ cudaError_t launch_fft_axis(double2 *data, int Lx, int Ly, int Lz, int axis, int
   dim3 grid((unsigned)((nlines + nl - 1) / nl), batch);
   if (sign > 0) {
     cudaFuncSetAttribute(k_fft_axis<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fft_axis<1><<<grid, threads, smem, st>>>(data, Lx, Ly, Lz, axis, lg, batch_stride, nl, tw);
+    k_fft_axis<1><<<grid, threads, smem, st>>>(data, Lx, Ly, Lz, axis, L, batch_stride, nl, tw);
   } else {
     cudaFuncSetAttribute(k_fft_axis<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fft_axis<-1><<<grid, threads, smem, st>>>(data, Lx, Ly, Lz, axis, lg, batch_stride, nl, tw);
+    k_fft_axis<-1><<<grid, threads, smem, st>>>(data, Lx, Ly, Lz, axis, L, batch_stride, nl, tw);
   }
   return cudaGetLastError();
 }

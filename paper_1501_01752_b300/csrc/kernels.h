@@ -11,7 +11,7 @@
 
 namespace gsm {
 
-constexpr int TWN_HOST = 256;  // twiddle table entries (largest FFT size)
+constexpr int TWN_HOST = 768;  // twiddle table entries: exp(2 pi i j / 768), every supported FFT size divides 768
 
 enum ProfKind { KIND_FWD_X = 0, KIND_YZ = 1, KIND_INV_X = 2, KIND_DOTS = 3, KIND_UPDATE = 4, KIND_OTHER = 5,
                 KIND_RESID64 = 6, KIND_COUNT = 7 };

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
   C *Tb = T + b * g.Tsz;
   const R s = scale ? scale[b] : (R)1;
   const long long Nh = g.Nh;
-  Team tm(g.lg[0]);
+  Team tm(g.L[0]);
   // Green tensor ingredients for the adjoint form (G applied before the
   // Toeplitz product; G is real symmetric for real k and k_b^2) and the wave
   // vector of the H-field form
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
       S[row * P0 + wrap(mx, g.n[0], L0)] = v;
     }
     __syncthreads();
-    for (int row = tm.id; row < nr; row += tm.count) team_fft<+1>(S + row * P0, g.lg[0], tm.lane, tm.ts, tm.mask, tw);
+    for (int row = tm.id; row < nr; row += tm.count) team_fft<+1>(S + row * P0, g.L[0], tm.lane, tm.ts, tm.mask, tw);
     __syncthreads();
     for (int e = threadIdx.x; e < nr * L0; e += blockDim.x) {
       const int rx = e / nr, row = e - rx * nr;
@@ -127,27 +127,27 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_yz(Geo g, typen
     A[mz * P1 + wrap(my, g.n[1], L1)] = Tb[e];
   }
   __syncthreads();
-  Team ty(g.lg[1]);
-  for (int row = ty.id; row < N2; row += ty.count) team_fft<+1>(A + row * P1, g.lg[1], ty.lane, ty.ts, ty.mask, tw);
+  Team ty(g.L[1]);
+  for (int row = ty.id; row < N2; row += ty.count) team_fft<+1>(A + row * P1, g.L[1], ty.lane, ty.ts, ty.mask, tw);
   __syncthreads();
-  Team tz(g.lg[2]);
-  C *bf = buf + tz.id * P2;
+  Team tz(g.L[2]);
   const R *Dx = D + (long long)rx * L1 * L2;
   for (int ry = tz.id; ry < L1; ry += tz.count) {
+    C *bf = buf + tz.id * P2;   // this team's column buffer
     for (int i = tz.lane; i < L2; i += tz.ts) bf[i] = czero<C>();
     __syncwarp(tz.mask);
     for (int mz = tz.lane; mz < N2; mz += tz.ts) bf[wrap(mz, g.n[2], L2)] = A[mz * P1 + ry];
     __syncwarp(tz.mask);
-    team_fft<+1>(bf, g.lg[2], tz.lane, tz.ts, tz.mask, tw);
+    team_fft<+1>(bf, g.L[2], tz.lane, tz.ts, tz.mask, tw);
     const R *Dc = Dx + (long long)ry * L2;
     for (int i = tz.lane; i < L2; i += tz.ts) bf[i] = cscale(bf[i], Dc[i]);
     __syncwarp(tz.mask);
-    team_fft<-1>(bf, g.lg[2], tz.lane, tz.ts, tz.mask, tw);
+    team_fft<-1>(bf, g.L[2], tz.lane, tz.ts, tz.mask, tw);
     for (int mz = tz.lane; mz < N2; mz += tz.ts) A[mz * P1 + ry] = bf[wrap(mz, g.n[2], L2)];
     __syncwarp(tz.mask);
   }
   __syncthreads();
-  for (int row = ty.id; row < N2; row += ty.count) team_fft<-1>(A + row * P1, g.lg[1], ty.lane, ty.ts, ty.mask, tw);
+  for (int row = ty.id; row < N2; row += ty.count) team_fft<-1>(A + row * P1, g.L[1], ty.lane, ty.ts, ty.mask, tw);
   __syncthreads();
   for (int e = threadIdx.x; e < N2 * N1; e += blockDim.x) {
     const int mz = e / N1, my = e - mz * N1;
@@ -196,9 +196,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
     for (int i = threadIdx.x; i < nr; i += blockDim.x) kys[i] = (R)(inst[b].kinc[1] + (my0 + i - g.n[1]) * g.K[1]);
   }
   __syncthreads();
-  Team tm(g.lg[0]);
+  Team tm(g.L[0]);
   for (int q = tm.id; q < 3 * rows; q += tm.count)
-    if (q % rows < nr) team_fft<-1>(S + q * P0, g.lg[0], tm.lane, tm.ts, tm.mask, tw);
+    if (q % rows < nr) team_fft<-1>(S + q * P0, g.L[0], tm.lane, tm.ts, tm.mask, tw);
   __syncthreads();
   const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
   const R kb2 = (R)inst[b].kb2;
