@@ -77,7 +77,9 @@ typedef struct gsm_plan_s gsm_plan_t;
 typedef struct {
   double period[3];     /* Lambda_x, Lambda_y, Lambda_z (> 0)                            */
   int n_harm[3];        /* N_x, N_y, N_z: odd, >= 1, <= 127                              */
-  int fft[3];           /* FFT points per axis; 0 = smallest power of two >= 2N-1 (<= 256) */
+  int fft[3];           /* FFT points per axis >= 2N-1: 0 = smallest power of two (<= 256);
+                           a power of two or 3 * 2^p in [24, 192] as given; -1 = tuned
+                           per level (see gsm_level_fft)                                 */
   double eps_b[2];      /* basis permittivity eps_b (re, im); im must be 0               */
   int precision;        /* GSM_FP64 or GSM_FP32_REFINE                                   */
   int krylov;           /* GSM_GMRES (basis of restart + 1 vectors per instance) or
@@ -227,6 +229,13 @@ gsm_status gsm_apply_noalloc(gsm_plan_t *plan, const gsm_point *point, const dou
  * first batch solved and the fastest is kept (256 before that, or with
  * GSM_AUTOTUNE=0 in the environment).  GSM_ERR_STATE before the first solve. */
 gsm_status gsm_tuned_blocks(const gsm_plan_t *plan, int precision, int blocks[3]);
+
+/* FFT grid (points per axis) of the level of truncation n_harm once it has
+ * been built by a call on points of that truncation: the plan's sizes, or,
+ * for axes given as fft = -1, the power of two or the smaller mixed-radix
+ * size 3 * 2^p, whichever ran one product of the batch faster when the level
+ * was first built.  GSM_ERR_STATE if the level does not exist yet. */
+gsm_status gsm_level_fft(const gsm_plan_t *plan, const int n_harm[3], int fft_out[3]);
 
 const char *gsm_last_error(const gsm_plan_t *plan);
 const char *gsm_version(void);

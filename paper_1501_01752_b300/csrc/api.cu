@@ -41,6 +41,17 @@ struct Level {
   dfl *Ddf = nullptr;       // D as double-float, for the outer residual (lane-team levels only)
   int tb[2][3] = {{256, 256, 256}, {256, 256, 256}};  // lane-team block sizes per pass, [FP64, complex64]
   bool tuned[2] = {false, false};
+  bool grid_chosen = false;  // FFT sizes fixed (by the plan, or timed once for fft = -1)
+  void free_multipliers() {
+    cudaFree(D64);
+    cudaFree(D32);
+    cudaFree(D32p);
+    cudaFree(Ddf);
+    D64 = nullptr;
+    D32 = nullptr;
+    D32p = nullptr;
+    Ddf = nullptr;
+  }
 };
 
 // Device workspace for one level, sized for B instances and a basis of m+1.
@@ -310,17 +321,14 @@ static gsm_status ensure_pinned(gsm_plan_t *p, size_t bytes) {
   return GSM_OK;
 }
 
-// Build D(r) for a level from the analytic coefficients (once per structure).
-static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
-  Key key{{N[0], N[1], N[2]}};
-  auto it = p->levels.find(key);
-  if (it != p->levels.end() && it->second.D64) {
-    *out = &it->second;
-    return GSM_OK;
-  }
-  if (!p->have_eps) return fail(p, GSM_ERR_STATE, "gsm_set_permittivity has not been called");
-  Level &lv = p->levels[key];
-  lv.g = make_geo(p->d, N, p->L);
+template <typename R>
+static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a, Profiler *prof,
+                          cudaStream_t st = nullptr);
+
+// D(r) of a level on its grid from the analytic coefficients (once per
+// structure): the multiplier in FP64 and FP32, its x-plane pairs and its
+// double-float copy where the lane-team product reads them.
+static gsm_status build_multiplier(gsm_plan_t *p, Level &lv) {
   const Geo &g = lv.g;
   const int D[3] = {2 * g.n[0], 2 * g.n[1], 2 * g.n[2]};
   std::vector<cd> eps;
@@ -377,6 +385,134 @@ static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
   }
   CK(cudaStreamSynchronize(p->st));
   cudaFree(dc);
+  return GSM_OK;
+}
+
+// One complex64 (or FP64) product of B zero instances on a level's grid,
+// timed with events (one warm-up, three timed launches): the FFT-grid tuner.
+template <typename R>
+static gsm_status time_product(gsm_plan_t *p, Level &lv, int B, float *ms) {
+  using C = typename Cx<R>::T;
+  const Geo &g = lv.g;
+  C *X = nullptr, *Y = nullptr, *T = nullptr;
+  Inst *inst = nullptr;
+  R *iden = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&]() {
+    cudaFree(X);
+    cudaFree(Y);
+    cudaFree(T);
+    cudaFree(inst);
+    cudaFree(iden);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&X, (size_t)B * g.U * sizeof(C)) != cudaSuccess ||
+      cudaMalloc(&Y, (size_t)B * g.U * sizeof(C)) != cudaSuccess ||
+      cudaMalloc(&T, (size_t)B * g.Tsz * sizeof(C)) != cudaSuccess ||
+      cudaMalloc(&inst, (size_t)B * sizeof(Inst)) != cudaSuccess ||
+      cudaMalloc(&iden, (size_t)B * g.Nh * sizeof(R)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(p, GSM_ERR_NOMEM, "FFT-grid tuner: probe allocation failed");
+  }
+  cudaMemsetAsync(X, 0, (size_t)B * g.U * sizeof(C), p->st);
+  cudaMemsetAsync(inst, 0, (size_t)B * sizeof(Inst), p->st);
+  cudaMemsetAsync(iden, 0, (size_t)B * g.Nh * sizeof(R), p->st);
+  MatvecArgs<R> a;
+  a.g = g;
+  a.B = B;
+  a.X = X;
+  a.xstride = g.U;
+  a.Y = Y;
+  a.ystride = g.U;
+  a.T = T;
+  if constexpr (sizeof(R) == 4) {
+    a.D = lv.D32;
+    a.Dp = lv.D32p;
+    a.tw = p->tw32;
+  } else {
+    a.D = lv.D64;
+    a.tw = p->tw64;
+  }
+  a.inst = inst;
+  a.iden = iden;
+  a.form = p->d.form;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t e = matvec<R>(p, lv, a, nullptr);
+  cudaEventRecord(e0, p->st);
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = matvec<R>(p, lv, a, nullptr);
+  cudaEventRecord(e1, p->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  release();
+  if (e != cudaSuccess) return fail(p, GSM_ERR_CUDA, std::string("FFT-grid tuner: ") + cudaGetErrorString(e));
+  p->launches += 12;
+  return GSM_OK;
+}
+
+// The level of truncation N, its multiplier built for the current structure.
+// Axes with fft = -1 in the plan take the power-of-two grid or the smaller
+// mixed-radix one (3 * 2^p), whichever runs one product of the batch faster
+// (timed once per level; the choice survives new permittivities).
+static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
+  Key key{{N[0], N[1], N[2]}};
+  auto it = p->levels.find(key);
+  if (it != p->levels.end() && it->second.D64) {
+    *out = &it->second;
+    return GSM_OK;
+  }
+  if (!p->have_eps) return fail(p, GSM_ERR_STATE, "gsm_set_permittivity has not been called");
+  Level &lv = p->levels[key];
+  gsm_status s;
+  if (!lv.grid_chosen) {
+    lv.g = make_geo(p->d, N, p->L);
+    Level alt;
+    alt.g = lv.g;
+    bool mixed = false;
+    for (int a = 0; a < 3; ++a)
+      if (p->d.fft[a] == -1) {
+        const int m = mixed_size(N[a]);
+        if (m) {
+          alt.g.L[a] = m;
+          mixed = true;
+        }
+      }
+    if (mixed) {
+      alt.g.Tsz = 3LL * alt.g.L[0] * alt.g.N[1] * alt.g.N[2];
+      if ((s = build_multiplier(p, lv)) || (s = build_multiplier(p, alt))) {
+        alt.free_multipliers();
+        return s;
+      }
+      const int B = std::max(1, std::min(32, batch_of(p->d)));
+      float t_pow2 = 0, t_mixed = 0;
+      if (p->d.precision == GSM_FP32_REFINE) {
+        if (!(s = time_product<float>(p, lv, B, &t_pow2))) s = time_product<float>(p, alt, B, &t_mixed);
+      } else {
+        if (!(s = time_product<double>(p, lv, B, &t_pow2))) s = time_product<double>(p, alt, B, &t_mixed);
+      }
+      if (s) {
+        alt.free_multipliers();
+        return s;
+      }
+      if (t_mixed < t_pow2) {
+        lv.free_multipliers();
+        lv.g = alt.g;
+        lv.D64 = alt.D64;
+        lv.D32 = alt.D32;
+        lv.D32p = alt.D32p;
+        lv.Ddf = alt.Ddf;
+      } else {
+        alt.free_multipliers();
+      }
+      lv.grid_chosen = true;
+      *out = &lv;
+      return GSM_OK;
+    }
+    lv.grid_chosen = true;
+  }
+  if ((s = build_multiplier(p, lv))) return s;
   *out = &lv;
   return GSM_OK;
 }
@@ -432,7 +568,7 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
 // shared-memory FFT kernels otherwise.
 template <typename R>
 static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a, Profiler *prof,
-                          cudaStream_t st = nullptr) {
+                          cudaStream_t st) {
   (void)lv;
   if (!st) st = p->st;
   if constexpr (std::is_same<R, dfl>::value) {
@@ -1389,6 +1525,14 @@ extern "C" gsm_status gsm_retrieve_tensor(gsm_plan_t *p, double k0, const double
       diag[4 * c + 3] = zeta[j].imag();
     }
   }
+  return GSM_OK;
+}
+
+extern "C" gsm_status gsm_level_fft(const gsm_plan_t *p, const int n_harm[3], int fft_out[3]) {
+  if (!p || !n_harm || !fft_out) return GSM_ERR_ARG;
+  auto it = p->levels.find(Key{{n_harm[0], n_harm[1], n_harm[2]}});
+  if (it == p->levels.end() || !it->second.grid_chosen) return GSM_ERR_STATE;
+  for (int a = 0; a < 3; ++a) fft_out[a] = it->second.g.L[a];
   return GSM_OK;
 }
 

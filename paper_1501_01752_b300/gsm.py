@@ -79,6 +79,7 @@ def _load():
         "gsm_retrieve_tensor_grad": (ct.c_int, [P, ct.c_double, dp, ct.c_int, ct.c_int, ct.c_int, dp, dp, dp]),
         "gsm_profile": (ct.c_int, [P, ct.c_int]),
         "gsm_tuned_blocks": (ct.c_int, [P, ct.c_int, ct.POINTER(ct.c_int)]),
+        "gsm_level_fft": (ct.c_int, [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
         "gsm_profile_get": (ct.c_int, [P, ct.c_int, ct.POINTER(ct.c_longlong), dp, dp]),
         "gsm_last_error": (ct.c_char_p, [P]),
         "gsm_version": (ct.c_char_p, []),
@@ -301,6 +302,13 @@ class Plan:
         s = lib.gsm_retrieve_tensor_grad(self.h, k0, _dp(lohi), n_kappa, Np, Nd, _dp(w), _dp(eps), _dp(out))
         self._check(s, "gsm_retrieve_tensor_grad")
         return eps, out.reshape(self.M)
+
+    def level_fft(self, n_harm=None):
+        """FFT grid of a built level (the tuned choice for fft = -1 axes)."""
+        N = (ct.c_int * 3)(*(n_harm or self.n_harm))
+        out = (ct.c_int * 3)()
+        self._check(lib.gsm_level_fft(self.h, N, out), "gsm_level_fft")
+        return tuple(out)
 
     def tuned_blocks(self, precision=FP32_REFINE):
         """Autotuned threads per block of the three product passes."""

@@ -67,3 +67,32 @@ def test_refined_solve_on_L48_matches_power_of_two_grid(krylov):
     ost = oracle_structure(st)
     E, _ = ort.solve_point(ost, n_harm, 1.0, pts[0]["k0"], pts[0]["kdir"], pts[0]["kappa"], pts[0]["pol"], tol=1e-12)
     assert rel(E48[:U], E.ravel()) < 1e-8
+
+
+def test_tuned_grid_choice_and_solution():
+    # fft = -1: each level times one product on the power-of-two grid and on
+    # the smaller mixed-radix one and keeps the faster; the fields do not
+    # depend on the choice, and the choice survives a new permittivity
+    g = gsm()
+    st = wl.ellipsoid_lattice()
+    pts = [wl.point((0.7 + 0.05 * i) * K0, (0, 0, 1), (1, 0, 0)) for i in range(4)]
+    ost = oracle_structure(st)
+    for N, cands in ((21, ((48,) * 3, (64,) * 3)), (41, ((96,) * 3, (128,) * 3))):
+        n_harm = (N, N, N)
+        plan = g.plan_for(st, n_harm, precision=g.FP32_REFINE, tol=1e-8, fft=(-1, -1, -1), max_batch=4)
+        with pytest.raises(g.GsmError):
+            plan.level_fft((9, 9, 9))              # a truncation no call has used yet
+        E, infos, s = plan.solve(pts)
+        L = plan.level_fft(n_harm)
+        assert s == 0 and L in cands, L
+        Delta = ost.delta(n_harm, 1.0)
+        U = 3 * N ** 3
+        for b, p in enumerate(pts[:2]):
+            A = oop.Operator(Delta, n_harm, p["kappa"] * np.asarray(p["kdir"]), st["periods"], p["k0"] ** 2)
+            bv = oop.incident(p["pol"], n_harm)
+            res = np.linalg.norm(bv - A(E[b * U:(b + 1) * U].reshape(bv.shape))) / np.linalg.norm(bv)
+            assert res <= 1.5e-8, (N, b, res)
+        plan.set_structure(wl.ellipsoid_lattice(eps=5.0))
+        plan.solve(pts[:1])
+        assert plan.level_fft(n_harm) == L
+        plan.close()
