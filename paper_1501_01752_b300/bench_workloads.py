@@ -162,12 +162,15 @@ def gyroid(args):
         plan = gsm.plan_for(st, (63, 63, 63), precision=prec, tol=1e-8, max_batch=1, hbm_cap=256 << 20,
                             max_iter=20000)
         E = torch.empty(U, dtype=torch.complex128, device="cuda")
-        a, b = _events()
-        a.record()
-        _, infos, s = plan.solve([pt], out=E)
-        b.record()
-        b.synchronize()
-        res[name] = dict(seconds=a.elapsed_time(b) / 1000, iters=infos[0]["iters"],
+        t = []
+        for _ in range(2):   # the first solve also loads kernels, tunes block sizes and captures graphs
+            a, b = _events()
+            a.record()
+            _, infos, s = plan.solve([pt], out=E)
+            b.record()
+            b.synchronize()
+            t.append(a.elapsed_time(b) / 1000)
+        res[name] = dict(seconds=t[1], first_solve_seconds=t[0], iters=infos[0]["iters"],
                          refine_steps=infos[0]["refine_steps"], rel_residual=infos[0]["rel_residual"],
                          status=infos[0]["status"])
         plan.close()

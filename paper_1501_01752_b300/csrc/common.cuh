@@ -32,6 +32,14 @@ template <typename R> struct Io { using T = typename Cx<R>::T; };
 template <typename C, typename IO> __device__ __forceinline__ C io_in(IO v) { return v; }
 template <typename IO, typename C> __device__ __forceinline__ IO io_out(C v) { return v; }
 
+// the value of the neighbouring lane (lane ^ 1) within the lanes of mask
+__device__ __forceinline__ float2 shfl_xor1(float2 v, unsigned mask) {
+  return make_float2(__shfl_xor_sync(mask, v.x, 1), __shfl_xor_sync(mask, v.y, 1));
+}
+__device__ __forceinline__ double2 shfl_xor1(double2 v, unsigned mask) {
+  return make_double2(__shfl_xor_sync(mask, v.x, 1), __shfl_xor_sync(mask, v.y, 1));
+}
+
 // read-only loads of twiddle-table entries
 __device__ __forceinline__ float2 ldg_c(const float2 *p) { return __ldg(p); }
 __device__ __forceinline__ double2 ldg_c(const double2 *p) { return __ldg(p); }

@@ -84,6 +84,11 @@ __device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
 __device__ __forceinline__ dfl &operator-=(dfl &a, dfl b) { return a = a - b; }
 __device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = a * b; }
 
+__device__ __forceinline__ dcx shfl_xor1(dcx v, unsigned mask) {
+  return mk(dfl(__shfl_xor_sync(mask, v.x.hi, 1), __shfl_xor_sync(mask, v.x.lo, 1)),
+            dfl(__shfl_xor_sync(mask, v.y.hi, 1), __shfl_xor_sync(mask, v.y.lo, 1)));
+}
+
 // twiddle-table load through the read-only path
 __device__ __forceinline__ dcx ldg_c(const dcx *p) {
   const float4 t = __ldg(reinterpret_cast<const float4 *>(p));

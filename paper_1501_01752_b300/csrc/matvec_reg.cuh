@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
   if (act && !act[b]) return;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
   const Lanes ln(TS);
-  C w[8];
+  C w[F::NTW];
   F::twiddles(w, ln.lane, twg);
   const long long nrows = 3LL * N2 * N1;
   const long long rbase = (long long)blockIdx.x * RB * RPT + ln.team;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
   const long long Nh = g.Nh;
   const Lanes ln(TS);
-  C w[8];
+  C w[F::NTW];
   F::twiddles(w, ln.lane, twg);
   const long long nrows = (long long)N2 * N1;
   const long long r = (long long)blockIdx.x * RB + ln.team;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
   // y forward: team per m_z row, straight from global memory
   {
     const Lanes ln(FY::TS);
-    C w[8];
+    C w[FY::NTW];
     FY::twiddles(w, ln.lane, twg);
     for (int r0 = 0; r0 < N2; r0 += NTY) {
       const int mz = r0 + ln.team;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
   // z forward, times D, z inverse: team per y-frequency column
   {
     const Lanes ln(FZ::TS);
-    C w[8];
+    C w[FZ::NTW];
     FZ::twiddles(w, ln.lane, twg);
     const R *Dx = D + (long long)rx * LY * LZ;
     for (int c0 = 0; c0 < LY; c0 += NTZ) {
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
   // y inverse: team per row, straight to global memory
   {
     const Lanes ln(FY::TS);
-    C w[8];
+    C w[FY::NTW];
     FY::twiddles(w, ln.lane, twg);
     for (int r0 = 0; r0 < N2; r0 += NTY) {
       const int mz = r0 + ln.team;
@@ -427,28 +427,29 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   R *kxs = reinterpret_cast<R *>(S3 + 3 * rows * P);
   R *kys = kxs + N0, *kzs = kys + rows;
   // epilogue mapping: warp per row (rows warp, warp + NW, ...), lane per
-  // x harmonic (N0 <= 31 on this path since 2 N0 - 1 <= L0 <= 64).  The
-  // first PF rows' inputs are fetched now, so their loads overlap the
+  // x harmonic mx = lane + 32 m, m < MXN (2 N0 - 1 <= L0, so N0 <= 32 MXN).
+  // The first PF rows' inputs are fetched now, so their loads overlap the
   // transforms below.
-  constexpr int NW = TT / 32, PF = 2;
+  constexpr int NW = TT / 32, PF = 2, MXN = L0 > 64 ? 2 : 1;
   const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-  const bool lane_ok = wl < N0;
   const IO *Xb = X + b * xstride;
-  C px[PF][3];
-  R pid[PF];
+  C px[PF][MXN][3];
+  R pid[PF][MXN];
 #pragma unroll
-  for (int i = 0; i < PF; ++i) {
-    const int row = warp + i * NW;
-    px[i][0] = px[i][1] = px[i][2] = mk((R)0, (R)0);
-    pid[i] = 0;
-    if (lane_ok && row < nr) {
-      const long long h = (r0 + row) * N0 + wl;
-      px[i][0] = io_in<C>(Xb[h]);
-      px[i][1] = io_in<C>(Xb[Nh + h]);
-      px[i][2] = io_in<C>(Xb[2 * Nh + h]);
-      pid[i] = iden[b * Nh + h];
+  for (int i = 0; i < PF; ++i)
+#pragma unroll
+    for (int m = 0; m < MXN; ++m) {
+      const int row = warp + i * NW, mx = wl + 32 * m;
+      px[i][m][0] = px[i][m][1] = px[i][m][2] = mk((R)0, (R)0);
+      pid[i][m] = 0;
+      if (mx < N0 && row < nr) {
+        const long long h = (r0 + row) * N0 + mx;
+        px[i][m][0] = io_in<C>(Xb[h]);
+        px[i][m][1] = io_in<C>(Xb[Nh + h]);
+        px[i][m][2] = io_in<C>(Xb[2 * Nh + h]);
+        pid[i][m] = iden[b * Nh + h];
+      }
     }
-  }
   for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (R)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
   for (int i = threadIdx.x; i < nr; i += blockDim.x) {
     const long long rr = r0 + i;
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   }
   {
     const Lanes ln(TS);
-    C w[8];
+    C w[F::NTW];
     F::twiddles(w, ln.lane, twg);
     const int c = ln.team / rows, row = ln.team - c * rows;
     const bool valid = c < 3 && row < nr;
@@ -482,8 +483,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   const long long h0 = ((long long)g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
   IO *Yb = Y + b * ystride;
   R acc = 0;   // this thread's share of ||y||^2 (a few harmonics), widened once
-  auto body = [&](int row, C y0, C y1, C y2, R id) {
-    const int mx = wl;
+  auto body = [&](int row, int mx, C y0, C y1, C y2, R id) {
     const long long h = (r0 + row) * N0 + mx;
     const C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
             u2 = S3[(2 * rows + row) * P + mx];
@@ -517,17 +517,22 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     Yb[Nh + h] = io_out<IO>(y1);
     Yb[2 * Nh + h] = io_out<IO>(y2);
   };
-  if (lane_ok) {
 #pragma unroll
-    for (int i = 0; i < PF; ++i) {
-      const int row = warp + i * NW;
-      if (row < nr) body(row, px[i][0], px[i][1], px[i][2], pid[i]);
+  for (int i = 0; i < PF; ++i)
+#pragma unroll
+    for (int m = 0; m < MXN; ++m) {
+      const int row = warp + i * NW, mx = wl + 32 * m;
+      if (row < nr && mx < N0) body(row, mx, px[i][m][0], px[i][m][1], px[i][m][2], pid[i][m]);
     }
-    for (int row = warp + PF * NW; row < nr; row += NW) {
-      const long long h = (r0 + row) * N0 + wl;
-      body(row, io_in<C>(Xb[h]), io_in<C>(Xb[Nh + h]), io_in<C>(Xb[2 * Nh + h]), iden[b * Nh + h]);
+  for (int row = warp + PF * NW; row < nr; row += NW)
+#pragma unroll
+    for (int m = 0; m < MXN; ++m) {
+      const int mx = wl + 32 * m;
+      if (mx < N0) {
+        const long long h = (r0 + row) * N0 + mx;
+        body(row, mx, io_in<C>(Xb[h]), io_in<C>(Xb[Nh + h]), io_in<C>(Xb[2 * Nh + h]), iden[b * Nh + h]);
+      }
     }
-  }
   if (norm_out) last_block_sum((double)acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
 }
 
@@ -537,9 +542,29 @@ static int p3_rows(const Geo &g, int tb) { return (tb / (g.L[0] / 8)) / 3; }
 
 constexpr int P1_RPT = 2;   // rows per team in pass 1
 
+// Threads per block of the 128-point kernels: their static team buffers
+// (TT / 16 teams x 144 values) stay under 48 KB for 16-byte values only up
+// to 256 threads.
+template <typename R, int TT>
+constexpr int tt128() { return (sizeof(typename Cx<R>::T) > 8 && TT > 256) ? 256 : TT; }
+
 template <typename R, int TT>
 static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
   const Geo &g = a.g;
+  if (g.L[0] == 128) {
+    constexpr int TX = tt128<R, TT>();
+    if (a.form) {
+      dim3 gridh((int)(((long long)g.N[2] * g.N[1] + TX / 16 - 1) / (TX / 16)), a.B);
+      k_fwd_x_t8h<R, 128, TX><<<gridh, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
+                                                    a.tw, a.jdev, a.jstride);
+    } else {
+      const int RB = TX / 16 * P1_RPT;
+      dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
+      k_fwd_x_t8<R, 128, TX, P1_RPT><<<grid, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act,
+                                                          a.tw, a.jdev, a.jstride);
+    }
+    return;
+  }
   const int RB = TT / (g.L[0] / 8) * P1_RPT;
   dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
   if (a.form) {
@@ -576,6 +601,12 @@ static void pass2(const MatvecArgs<R> &a, cudaStream_t st) {
   }
   const size_t smem = sizeof(C) * (size_t)g.N[2] * g.L[1];
   dim3 grid(g.L[0], 3, a.B);
+  if (g.L[1] == 128 && g.L[2] == 128) {
+    constexpr int TX = tt128<R, TT>();
+    cudaFuncSetAttribute(k_yz_t8<R, 128, 128, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_yz_t8<R, 128, 128, TX><<<grid, TX, smem, st>>>(g, a.T, a.D, a.act, a.tw);
+    return;
+  }
 #define GSM_YZ(LY, LZ)                                                                                      \
   cudaFuncSetAttribute(k_yz_t8<R, LY, LZ, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
   k_yz_t8<R, LY, LZ, TT><<<grid, TT, smem, st>>>(g, a.T, a.D, a.act, a.tw)
@@ -590,6 +621,21 @@ template <typename R, int TT>
 static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   using C = typename Cx<R>::T;
   const Geo &g = a.g;
+  if (g.L[0] == 128) {
+    constexpr int TX = tt128<R, TT>();
+    const int rows = p3_rows(g, TX);
+    const size_t smem = sizeof(C) * 3 * (size_t)rows * p3_pitch(g.N[0]) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
+    dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);
+#define GSM_P3X(M, HF)                                                                                           \
+  cudaFuncSetAttribute(k_inv_x_t8<R, 128, M, TX, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+  k_inv_x_t8<R, 128, M, TX, HF><<<grid, TX, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,   \
+                                                        a.iden, a.tw, rows, a.partial, a.counter, a.norm_out,     \
+                                                        a.jdev, a.jstride)
+    if (a.form) { if (a.mode == 1) { GSM_P3X(1, 1); } else { GSM_P3X(0, 1); } }
+    else { if (a.mode == 1) { GSM_P3X(1, 0); } else { GSM_P3X(0, 0); } }
+#undef GSM_P3X
+    return;
+  }
   const int rows = p3_rows(g, TT);
   const size_t smem = sizeof(C) * 3 * (size_t)rows * p3_pitch(g.N[0]) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
   dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);

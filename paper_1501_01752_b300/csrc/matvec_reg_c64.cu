@@ -23,6 +23,7 @@ bool packed_yz_ok(const Geo &g) { return g.L[1] == 64 && g.L[2] == 64 && g.L[0] 
 
 bool reg_path_ok(const Geo &g) {
   auto ok = [](int L) { return L == 32 || L == 64; };
+  if (g.L[0] == 128 && g.L[1] == 128 && g.L[2] == 128) return true;   // 16-lane teams, cubic grids only
   return ok(g.L[0]) && ok(g.L[1]) && ok(g.L[2]);
 }
 
