@@ -35,6 +35,18 @@ template <int L> struct Team8 {
                     : (TS == 8 ? lane + 8 * r : (lane + 4 * (r / 4)) + 8 * (r % 4));
   }
 
+  // freq(lane, r) - freq(lane, 0): the same for every lane, so the stores of
+  // one lane's spectral values are one base address plus constant offsets
+  __host__ __device__ static constexpr int fstep(int r) {
+    return TS == 4 ? 4 * (r / 4) + 8 * (r % 4) : 8 * r;
+  }
+  __host__ __device__ static constexpr bool fstep_ok() {
+    for (int l = 0; l < TS; ++l)
+      for (int r = 0; r < 8; ++r)
+        if (freq(l, r) - freq(l, 0) != fstep(r)) return false;
+    return true;
+  }
+
   // lane twiddles w_L^{lane k} (k < 8; for TS = 16 also the inverse set)
   // from the TWN-entry table in global memory (6 or 12 KB: it stays in L1
   // after the first warps touch it)

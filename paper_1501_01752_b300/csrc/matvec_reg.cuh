@@ -43,9 +43,44 @@ struct Lanes {
   }
 };
 
+// q = r / d and rem = r - q d for 0 <= r < 2^22, 0 < d <= 256, with rd the
+// FP32 reciprocal of d: the truncated estimate r rd is within one of q
+// (relative error below 2^-23 on a quotient below 2^22 / d) and is corrected
+// once, in place of an integer division.
+__device__ __forceinline__ int divmod_small(int r, int d, float rd, int &rem) {
+  int q = __float2int_rz((float)r * rd);
+  int m = r - q * d;
+  if (m < 0) {
+    --q;
+    m += d;
+  } else if (m >= d) {
+    ++q;
+    m -= d;
+  }
+  rem = m;
+  return q;
+}
+
+// Harmonic offsets of a lane's natural positions k = lane + TS a.  Harmonics
+// m in [-n, n] sit at m mod L with L >= 4 n + 4 (every lane-team grid: L is
+// a multiple of 4 and >= 2 N - 1 = 4 n + 1), so only a in {0, 1, 6, 7} can
+// hold one: slot j = 0..3 stands for a = 0, 1, 6, 7, and off[j] is the
+// harmonic index (0..N-1) there or -1.
+template <int L, int TS> struct HarmSlots {
+  int off[4];
+  __device__ __forceinline__ HarmSlots(int lane, int n) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = lane + TS * (j < 2 ? j : j + 4);
+      off[j] = j < 2 ? (k <= n ? k + n : -1) : (k >= L - n ? k - L + n : -1);
+    }
+  }
+  __host__ __device__ static constexpr int slot(int a) { return a < 2 ? a : (a >= 6 ? a - 4 : -1); }
+};
+
 // Each team transforms RPT rows (RB rows apart), issuing the loads of all of
 // them before the first transform, so that more reads are in flight per
-// thread.
+// thread.  Row indices are 32-bit (3 N1 N2 < 2^22 rows per instance).
 template <typename R, int L0, int TT, int RPT>
 __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__restrict__ X, long long xstride,
                                                  typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
@@ -55,34 +90,38 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
   using C = typename Cx<R>::T;
   using IO = typename Io<R>::T;
   using F = Team8<L0>;
+  static_assert(F::fstep_ok(), "spectral layout must be a lane base plus constant steps");
   if (jdev) X += (long long)(*jdev) * jstride;
   constexpr int TS = F::TS, RB = TT / TS;
   __shared__ C bufs[RB * F::BUF];
   const int b = blockIdx.y;
   if (act && !act[b]) return;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
+  const int P = N2 * N1, nrows = 3 * P;
+  const float rN1 = 1.0f / (float)N1, rN2 = 1.0f / (float)N2;
   const Lanes ln(TS);
   C w[F::NTW];
   F::twiddles(w, ln.lane, twg);
-  const long long nrows = 3LL * N2 * N1;
-  const long long rbase = (long long)blockIdx.x * RB * RPT + ln.team;
+  const HarmSlots<L0, TS> hs(ln.lane, g.n[0]);
+  const int rbase = blockIdx.x * RB * RPT + ln.team;
   const R s = scale ? scale[b] : (R)1;
+  IO *Xb = X + b * xstride;
   C v[RPT][8];
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
-    const long long r = rbase + (long long)i * RB;
+    const int r = rbase + i * RB;
     const bool valid = r < nrows;
-    const IO *Xr = X + b * xstride + r * N0;
+    const IO *Xr = Xb + r * N0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
       v[i][a] = mk((R)0, (R)0);
-      if (valid && h >= 0) v[i][a] = io_in<C>(Xr[h]);
+      const int j = HarmSlots<L0, TS>::slot(a);
+      if (j >= 0 && valid && hs.off[j] >= 0) v[i][a] = io_in<C>(Xr[hs.off[j]]);
     }
   }
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
-    const long long r = rbase + (long long)i * RB;
+    const int r = rbase + i * RB;
     const bool valid = r < nrows;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -90,23 +129,21 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
       v[i][a].y *= s;
     }
     if (write_back && valid) {
-      IO *Xr = X + b * xstride + r * N0;
+      IO *Xr = Xb + r * N0;
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
-        if (h >= 0) Xr[h] = io_out<IO>(v[i][a]);
+        const int j = HarmSlots<L0, TS>::slot(a);
+        if (j >= 0 && hs.off[j] >= 0) Xr[hs.off[j]] = io_out<IO>(v[i][a]);
       }
     }
     F::template forward<+1>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
     if (!valid) continue;
-    const int plane = (int)(r / N1), my = (int)(r - (long long)plane * N1);
-    const int c = plane / N2, mz = plane - c * N2;
-    C *Tb = T + b * g.Tsz + (long long)mz * N1 + my;
+    int my, mz;
+    const int plane = divmod_small(r, N1, rN1, my);
+    const int c = divmod_small(plane, N2, rN2, mz);
+    C *Tq = T + b * g.Tsz + ((3 * F::freq(ln.lane, 0) + c) * P + mz * N1 + my);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int rx = F::freq(ln.lane, q);
-      Tb[((long long)rx * 3 + c) * N2 * N1] = v[i][q];
-    }
+    for (int q = 0; q < 8; ++q) Tq[F::fstep(q) * 3 * P] = v[i][q];
   }
 }
 
@@ -130,32 +167,35 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
   const int b = blockIdx.y;
   if (act && !act[b]) return;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
-  const long long Nh = g.Nh;
+  const int Nh = (int)g.Nh, P = N2 * N1;
   const Lanes ln(TS);
   C w[F::NTW];
   F::twiddles(w, ln.lane, twg);
-  const long long nrows = (long long)N2 * N1;
-  const long long r = (long long)blockIdx.x * RB + ln.team;
-  const bool valid = r < nrows;
+  const HarmSlots<L0, TS> hs(ln.lane, g.n[0]);
+  const int r = blockIdx.x * RB + ln.team;
+  const bool valid = r < P;
   const R s = scale ? scale[b] : (R)1;
-  const int mz = (int)(r / N1), my = (int)(r - (long long)mz * N1);
+  int my;
+  const int mz = divmod_small(r, N1, 1.0f / (float)N1, my);
   const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
   const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
   IO *Xr = X + b * xstride + r * N0;
   C v[3][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
+    const int j = HarmSlots<L0, TS>::slot(a);
 #pragma unroll
     for (int c = 0; c < 3; ++c) v[c][a] = mk((R)0, (R)0);
-    if (valid && h >= 0) {
+    if (j >= 0 && valid && hs.off[j] >= 0) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) v[c][a] = io_in<C>(Xr[c * Nh + h]);
+      for (int c = 0; c < 3; ++c) v[c][a] = io_in<C>(Xr[c * Nh + hs.off[j]]);
     }
   }
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
+    const int j = HarmSlots<L0, TS>::slot(a);
+    if (j < 0) continue;   // no harmonic here: v = 0 and so is k x v
+    const int h = hs.off[j];
     const R kx = (R)(inst[b].kinc[0] + (h - g.n[0]) * g.K[0]);
     C u[3];
 #pragma unroll
@@ -168,13 +208,13 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
     v[1][a] = csub(cscale(u[0], kz), cscale(u[2], kx));
     v[2][a] = csub(cscale(u[1], kx), cscale(u[0], ky));
   }
-  C *Tb = T + b * g.Tsz + (long long)mz * N1 + my;
+  C *Tq = T + b * g.Tsz + (3 * F::freq(ln.lane, 0) * P + mz * N1 + my);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     F::template forward<+1>(v[c], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
     if (valid)
 #pragma unroll
-      for (int q = 0; q < 8; ++q) Tb[((long long)F::freq(ln.lane, q) * 3 + c) * N2 * N1] = v[c][q];
+      for (int q = 0; q < 8; ++q) Tq[(F::fstep(q) * 3 + c) * P] = v[c][q];
   }
 }
 
@@ -420,10 +460,9 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   const int b = blockIdx.y;
   if (act && !act[b]) return;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2], P = p3_pitch(N0);
-  const long long Nh = g.Nh;
-  const long long r0 = (long long)blockIdx.x * rows;
-  const long long left = (long long)N1 * N2 - r0;
-  const int nr = (int)(left < rows ? left : rows);
+  const int Nh = (int)g.Nh, P2 = N1 * N2;   // 32-bit offsets: 3 Nh < 2^22
+  const int r0 = blockIdx.x * rows;
+  const int nr = min(rows, P2 - r0);
   R *kxs = reinterpret_cast<R *>(S3 + 3 * rows * P);
   R *kys = kxs + N0, *kzs = kys + rows;
   // epilogue mapping: warp per row (rows warp, warp + NW, ...), lane per
@@ -443,17 +482,17 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       px[i][m][0] = px[i][m][1] = px[i][m][2] = mk((R)0, (R)0);
       pid[i][m] = 0;
       if (mx < N0 && row < nr) {
-        const long long h = (r0 + row) * N0 + mx;
+        const int h = (r0 + row) * N0 + mx;
         px[i][m][0] = io_in<C>(Xb[h]);
         px[i][m][1] = io_in<C>(Xb[Nh + h]);
         px[i][m][2] = io_in<C>(Xb[2 * Nh + h]);
-        pid[i][m] = iden[b * Nh + h];
+        pid[i][m] = iden[(long long)b * Nh + h];
       }
     }
   for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (R)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
   for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-    const long long rr = r0 + i;
-    const int mz = (int)(rr / N1), my = (int)(rr - (long long)mz * N1);
+    int my;
+    const int mz = divmod_small(r0 + i, N1, 1.0f / (float)N1, my);
     kys[i] = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
     kzs[i] = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
   }
@@ -463,28 +502,28 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     F::twiddles(w, ln.lane, twg);
     const int c = ln.team / rows, row = ln.team - c * rows;
     const bool valid = c < 3 && row < nr;
-    const C *Tr = T + b * g.Tsz + r0 + row;
+    const C *Tq = T + b * g.Tsz + ((3 * F::freq(ln.lane, 0) + c) * P2 + r0 + row);
     C v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int rx = F::freq(ln.lane, q);
-      v[q] = valid ? Tr[((long long)rx * 3 + c) * N2 * N1] : mk((R)0, (R)0);
-    }
+    for (int q = 0; q < 8; ++q) v[q] = valid ? Tq[F::fstep(q) * 3 * P2] : mk((R)0, (R)0);
     F::template inverse<-1>(v, ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
-    if (valid)
+    if (valid) {
+      const HarmSlots<L0, TS> hs(ln.lane, g.n[0]);
+      C *Sr = S3 + (c * rows + row) * P;
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        const int h = harm_at(ln.lane + TS * a, g.n[0], L0);
-        if (h >= 0) S3[(c * rows + row) * P + h] = v[a];
+        const int j = HarmSlots<L0, TS>::slot(a);
+        if (j >= 0 && hs.off[j] >= 0) Sr[hs.off[j]] = v[a];
       }
+    }
   }
   __syncthreads();
   const R kb2 = (R)inst[b].kb2;
-  const long long h0 = ((long long)g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
+  const int h0 = (g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
   IO *Yb = Y + b * ystride;
   R acc = 0;   // this thread's share of ||y||^2 (a few harmonics), widened once
   auto body = [&](int row, int mx, C y0, C y1, C y2, R id) {
-    const long long h = (r0 + row) * N0 + mx;
+    const int h = (r0 + row) * N0 + mx;
     const C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
             u2 = S3[(2 * rows + row) * P + mx];
     const R kx = kxs[mx], ky = kys[row], kz = kzs[row];
@@ -529,8 +568,8 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     for (int m = 0; m < MXN; ++m) {
       const int mx = wl + 32 * m;
       if (mx < N0) {
-        const long long h = (r0 + row) * N0 + mx;
-        body(row, mx, io_in<C>(Xb[h]), io_in<C>(Xb[Nh + h]), io_in<C>(Xb[2 * Nh + h]), iden[b * Nh + h]);
+        const int h = (r0 + row) * N0 + mx;
+        body(row, mx, io_in<C>(Xb[h]), io_in<C>(Xb[Nh + h]), io_in<C>(Xb[2 * Nh + h]), iden[(long long)b * Nh + h]);
       }
     }
   if (norm_out) last_block_sum((double)acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
