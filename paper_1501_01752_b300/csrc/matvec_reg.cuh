@@ -326,6 +326,11 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
 // 32 banks evenly.
 __host__ __device__ __forceinline__ int p3_pitch(int N0) { return (N0 + 15) / 16 * 16 + 8; }
 
+// (component, row) items per lane team in pass 3: two for 32/64-point teams
+// (twice the loads in flight per thread), one for the 128-point teams, whose
+// registers are already taken by the longer transforms
+template <int L0> __host__ __device__ constexpr int p3_items() { return L0 <= 64 ? 2 : 1; }
+
 // Pass 2 for complex64 with 64-point y and z transforms, two x frequencies
 // (r_x, r_x + 1) per block: every lane runs the transforms of both planes at
 // once in packed FP32 pairs (Team8x2).  The plane buffer holds value pairs
@@ -452,7 +457,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     X += (long long)(*jdev) * jstride;
     Y += (long long)(*jdev) * jstride;
   }
-  constexpr int TS = F::TS, NTM = TT / TS;
+  constexpr int TS = F::TS, NTM = TT / TS, IPT = p3_items<L0>();
   __shared__ C bufs[NTM * F::BUF];
   __shared__ double red[32];
   extern __shared__ __align__(16) unsigned char sm_dyn[];
@@ -497,23 +502,35 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     kzs[i] = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
   }
   {
+    // team items (c, row) = divmod(team + i NTM, rows), i < IPT: the loads of
+    // all of a team's items are issued before its first transform
     const Lanes ln(TS);
     C w[F::NTW];
     F::twiddles(w, ln.lane, twg);
-    const int c = ln.team / rows, row = ln.team - c * rows;
-    const bool valid = c < 3 && row < nr;
-    const C *Tq = T + b * g.Tsz + ((3 * F::freq(ln.lane, 0) + c) * P2 + r0 + row);
-    C v[8];
+    C v[IPT][8];
+    int it_c[IPT], it_row[IPT];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = valid ? Tq[F::fstep(q) * 3 * P2] : mk((R)0, (R)0);
-    F::template inverse<-1>(v, ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
-    if (valid) {
-      const HarmSlots<L0, TS> hs(ln.lane, g.n[0]);
-      C *Sr = S3 + (c * rows + row) * P;
+    for (int i = 0; i < IPT; ++i) {
+      const int item = ln.team + i * NTM;
+      const int c = item / rows, row = item - c * rows;
+      it_c[i] = c;
+      it_row[i] = row;
+      const bool valid = c < 3 && row < nr;
+      const C *Tq = T + b * g.Tsz + ((3 * F::freq(ln.lane, 0) + c) * P2 + r0 + row);
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int j = HarmSlots<L0, TS>::slot(a);
-        if (j >= 0 && hs.off[j] >= 0) Sr[hs.off[j]] = v[a];
+      for (int q = 0; q < 8; ++q) v[i][q] = valid ? Tq[F::fstep(q) * 3 * P2] : mk((R)0, (R)0);
+    }
+    const HarmSlots<L0, TS> hs(ln.lane, g.n[0]);
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      F::template inverse<-1>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
+      if (it_c[i] < 3 && it_row[i] < nr) {
+        C *Sr = S3 + (it_c[i] * rows + it_row[i]) * P;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int j = HarmSlots<L0, TS>::slot(a);
+          if (j >= 0 && hs.off[j] >= 0) Sr[hs.off[j]] = v[i][a];
+        }
       }
     }
   }
@@ -576,7 +593,10 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
 }
 
 
-static int p3_rows(const Geo &g, int tb) { return (tb / (g.L[0] / 8)) / 3; }
+static int p3_rows(const Geo &g, int tb) {
+  const int items = (tb / (g.L[0] / 8)) * (g.L[0] <= 64 ? p3_items<64>() : p3_items<128>());
+  return items / 3;
+}
 
 
 constexpr int P1_RPT = 2;   // rows per team in pass 1
