@@ -49,9 +49,9 @@ OWN_MV = 8 * (_U + _TSZ) + 16 * _TSZ + 8 * (_TSZ + 2 * _U) + 4 * N_HARM[0] ** 3
 # dram__bytes_read.sum + dram__bytes_write.sum of the three product kernels
 # for one product launch at the bench batch (128 instances), from the ncu
 # capture summarised in profiles/traffic_c64_product_woodpile31_batch128.md
-# (x-forward 310.8 MB + yz 321.1 MB + x-inverse/Green 366.0 MB); None once a
-# product kernel changes after that capture
-NCU_TRAFFIC = 0.9979e9
+# (mean of two products: 915.1 and 910.1 MB); None once a product kernel
+# changes after that capture
+NCU_TRAFFIC = 0.9126e9
 
 
 def peaks():
@@ -186,6 +186,8 @@ def main():
                     help="Krylov method of the refined solve (and of the FP64 plain path)")
     ap.add_argument("--residual", default="auto", choices=["auto", "fp64"],
                     help="outer-residual arithmetic of the refined solve (double-float where available, or FP64)")
+    ap.add_argument("--precond", default="auto", choices=["auto", "none"],
+                    help="averaged-medium right preconditioner of the Krylov solves (auto) or none")
     ap.add_argument("--workload", default="woodpile",
                     choices=["woodpile", "matvec", "sweep", "gyroid", "adjoint", "optimise"])
     args = ap.parse_args()
@@ -214,7 +216,8 @@ def main():
                             stream=stream.cuda_stream, inner_tol=args.inner_tol,
                             krylov=gsm.BICGSTAB if args.krylov == "bicgstab" else gsm.GMRES,
                             form=gsm.FORM_H if args.form == "h" else gsm.FORM_E,
-                            residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO)
+                            residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO,
+                            precond=gsm.PRECOND_NONE if args.precond == "none" else gsm.PRECOND_AUTO)
 
     plan = make_plan(gsm.FP32_REFINE)
     E = torch.empty(B * U, dtype=torch.complex128, device=dev)
@@ -281,7 +284,7 @@ def main():
     for _ in range(ee_steps):
         plan.solve(pts, host_out=Eh)
     e2e = B * ws * ee_steps / (time.perf_counter() - t0)
-    h2d = B * 88  # instance parameters (kinc, k_b^2, polarisation) per point
+    h2d = B * 96  # per-point parameter block copied to the device: k_inc, k_b^2, polarisation, preconditioner (12 doubles)
     d2h = B * U * 16
 
     # the other Krylov method on the same batch (few steps; not the headline)
@@ -292,7 +295,8 @@ def main():
                             stream=stream.cuda_stream, inner_tol=args.inner_tol,
                             form=gsm.FORM_H if args.form == "h" else gsm.FORM_E,
                             krylov=gsm.BICGSTAB if alt == "bicgstab" else gsm.GMRES,
-                            residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO)
+                            residual=gsm.RESID_FP64 if args.residual == "fp64" else gsm.RESID_AUTO,
+                            precond=gsm.PRECOND_NONE if args.precond == "none" else gsm.PRECOND_AUTO)
         palt.solve(pts, out=E)
         talt, infos_alt = timed(palt, args.alt_steps, E)
         alt_line = {"krylov": alt, "value": B * args.alt_steps / talt, "unit": "solves/s",
@@ -319,9 +323,11 @@ def main():
     plan.apply(pts, xd, precision=gsm.FP32_REFINE)
     plan.profile(True)
     R_MV = 5
+    torch.cuda.nvtx.range_push("roofline_product")   # lets ncu select these launches (--nvtx-include)
     for _ in range(R_MV):
         plan.apply(pts, xd, precision=gsm.FP32_REFINE)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     mvk = {name: plan.profile_get(k) for k, name in enumerate(["fwd_x", "yz_conv", "inv_x_green"])}
     plan.profile(False)
     n_mv = mvk["fwd_x"][0]
@@ -342,6 +348,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec + c128 refinement", "data": "synthetic",
         "config": {"workload": "woodpile eps 11.9 in eps_b 1, Lambda 0.35, 31^3 harmonics, 64^3 FFT grid",
                    "global_batch": B * ws, "tol": TOL, "krylov": args.krylov, "form": args.form.upper(),
+                   "precond": args.precond,
                    "l2": "flushed between steps (inputs+basis > L2)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "fp64_plain": None if fp64_value is None else

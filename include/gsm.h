@@ -68,6 +68,13 @@ enum { GSM_RESID_AUTO = 0, GSM_RESID_FP64 = 1 };
  * incident H amplitude and the output field is H) */
 enum { GSM_FORM_E = 0, GSM_FORM_H = 1 };
 enum { GSM_GMRES = 0, GSM_BICGSTAB = 1 };            /* Krylov method            */
+/* GMRES on Eq. 4 with the lane-team product (FFT sizes 32/64, cubic 128):
+ * right preconditioner M = I - s Delta_0 G(m), the block diagonal of Eq. 4
+ * (the Green tensor of the cell-averaged medium, inverted in closed form per
+ * harmonic; s in {1, 1/2, 1/4, 1/8} per point keeps M away from singular,
+ * s = 0 when no choice does), or none.  The solution is the same; only the
+ * number of Krylov steps changes.  Not in the paper. */
+enum { GSM_PRECOND_AUTO = 0, GSM_PRECOND_NONE = 1 };
 enum { GSM_SPHERE = 0, GSM_BOX = 1, GSM_ELLIPSOID = 2 };
 
 typedef struct gsm_plan_s gsm_plan_t;
@@ -94,6 +101,7 @@ typedef struct {
   void *cuda_stream;    /* cudaStream_t to issue work on; NULL = default stream          */
   int residual;         /* GSM_RESID_AUTO or GSM_RESID_FP64 (refined solves)             */
   int form;             /* GSM_FORM_E (Eq. 4) or GSM_FORM_H (Eq. 5)                      */
+  int precond;          /* GSM_PRECOND_AUTO (GMRES on Eq. 4, lane-team levels) or NONE    */
 } gsm_plan_desc;
 
 /* Non-overlapping inclusion in the host medium (GSM section: analytic Fourier

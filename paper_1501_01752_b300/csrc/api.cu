@@ -42,6 +42,7 @@ struct Level {
   int tb[2][3] = {{256, 256, 256}, {256, 256, 256}};  // lane-team block sizes per pass, [FP64, complex64]
   bool tuned[2] = {false, false};
   bool grid_chosen = false;  // FFT sizes fixed (by the plan, or timed once for fft = -1)
+  double delta0 = 0;         // (Delta eps / eps_b)_0 of Eq. 4: the averaged medium of the preconditioner
   void free_multipliers() {
     cudaFree(D64);
     cudaFree(D32);
@@ -73,7 +74,7 @@ struct Work {
   KrylovPtrs k{};
   // a captured cycle holds its kernels' arguments by value, among them the
   // level's multiplier (D, Dp): it is reused only while those are unchanged
-  struct Cycle { int B, m, adj, force, prec; const void *D, *Dp; cudaGraph_t graph; cudaGraphExec_t exec; };
+  struct Cycle { int B, m, adj, force, prec, pc; const void *D, *Dp; cudaGraph_t graph; cudaGraphExec_t exec; };
   std::vector<Cycle> cycles;
   void drop_graphs() {
     for (auto &c : cycles) {
@@ -172,6 +173,8 @@ static std::string check_desc(const gsm_plan_desc *d, int L[3]) {
   if (d->krylov != GSM_GMRES && d->krylov != GSM_BICGSTAB) return "krylov must be GSM_GMRES or GSM_BICGSTAB";
   if (d->residual != GSM_RESID_AUTO && d->residual != GSM_RESID_FP64) return "residual must be GSM_RESID_AUTO or GSM_RESID_FP64";
   if (d->form != GSM_FORM_E && d->form != GSM_FORM_H) return "form must be GSM_FORM_E or GSM_FORM_H";
+  if (d->precond != GSM_PRECOND_AUTO && d->precond != GSM_PRECOND_NONE)
+    return "precond must be GSM_PRECOND_AUTO or GSM_PRECOND_NONE";
   if (d->restart < 0 || d->restart > 120) return "restart must be in [0, 120]";
   if (d->max_batch < 0 || d->max_batch > 4096) return "max_batch must be in [0, 4096]";
   return "";
@@ -358,6 +361,7 @@ static gsm_status build_multiplier(gsm_plan_t *p, Level &lv) {
     if (!p->vox.empty()) voxel_coefficients(p->vox.data(), p->M, D, eps);
     else shapes_coefficients(p->eps_host, p->shapes.data(), (int)p->shapes.size(), p->d.period, D, eps);
     eps[c0] -= eb;  // Delta eps = eps - eps_b at d = 0
+    lv.delta0 = (eps[c0] / eb).real();
   }
   const size_t LL = (size_t)g.L[0] * g.L[1] * g.L[2];
   std::vector<double2> grid(LL, make_double2(0.0, 0.0));
@@ -532,6 +536,8 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
   for (int a = 0; a < 3; ++a) I.kinc[a] = pt.kappa * pt.kdir[a] / nrm;
   I.kb2 = pt.k0 * pt.k0 * p->d.eps_b[0];
   for (int i = 0; i < 6; ++i) I.a[i] = pt.pol[i];
+  I.pc_c = 0.0;     // preconditioner off (identity) unless the solve sets it
+  I.pc_beta = 1.0;
   // Eq. 4 needs k_m^2 != k_b^2 for every harmonic (text after Eq. 4).  Along
   // each (m_y, m_z) row, k_m^2 - k_b^2 = (kx0 + m_x K_x)^2 - (k_b^2 - c) is a
   // parabola in m_x, closest to zero at the one or two m_x nearest the roots
@@ -563,6 +569,54 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
   return GSM_OK;
 }
 
+// Smallest |k_m^2 - T| over the harmonic box.  Along each (m_y, m_z) row,
+// k_m^2 - T = (kx0 + m_x K_x)^2 - (T - c) is a parabola in m_x, so only the
+// m_x nearest its roots (or its vertex) can be closest; they are clamped
+// to the box, where the parabola is monotone beyond them.
+static double min_gap(const Inst &I, const Geo &g, double T) {
+  double best = INFINITY;
+  for (int mz = -g.n[2]; mz <= g.n[2]; ++mz)
+    for (int my = -g.n[1]; my <= g.n[1]; ++my) {
+      const double ky = I.kinc[1] + my * g.K[1], kz = I.kinc[2] + mz * g.K[2];
+      const double c = ky * ky + kz * kz, r2 = T - c;
+      const double targets[2] = {r2 > 0 ? std::sqrt(r2) : 0.0, r2 > 0 ? -std::sqrt(r2) : 0.0};
+      for (int t = 0; t < 2; ++t) {
+        const int m0 = (int)std::floor((targets[t] - I.kinc[0]) / g.K[0]);
+        for (int d = -1; d <= 2; ++d) {
+          const int mx = std::min(g.n[0], std::max(-g.n[0], m0 + d));
+          const double kx = I.kinc[0] + mx * g.K[0];
+          best = std::min(best, std::fabs(kx * kx + c - T));
+        }
+      }
+    }
+  return best;
+}
+
+// Right preconditioner of the refined and FP64 GMRES solves (not in the
+// paper, which iterates on Eq. 4 as it stands): M = I - s Delta_0 G(m), the
+// block diagonal of Eq. 4 (the m - m' = 0 term of the Toeplitz product, i.e.
+// the Green tensor of the cell-averaged medium).  With G = g k_b^2 P_T - P_L
+// (g = 1/(k_m^2 - k_b^2), P_L = k k^T / k^2, P_T = I - P_L) its inverse is
+// alpha P_T + beta P_L, alpha = (k_m^2 - k_b^2) / (k_m^2 - k_b^2 (1 + s Delta_0)),
+// beta = 1 / (1 + s Delta_0).  M is singular where a harmonic lies on the
+// light cone of the averaged medium, so s is the largest of 1, 1/2, 1/4, 1/8
+// that keeps every |k_m^2 - k_b^2 (1 + s Delta_0)| >= 0.1 s |Delta_0| k_b^2
+// (|alpha - 1| <= 10) and 1 + s Delta_0 >= 0.1; 0 (no preconditioner) if
+// none does.
+static void set_precond(Inst &I, const Geo &g, double d0) {
+  I.pc_c = 0.0;
+  I.pc_beta = 1.0;
+  if (!(std::fabs(d0) > 0) || !std::isfinite(d0)) return;
+  for (double s = 1.0; s >= 0.125; s *= 0.5) {
+    const double sd = s * d0;
+    if (1.0 + sd < 0.1) continue;
+    if (min_gap(I, g, I.kb2 * (1.0 + sd)) < 0.1 * std::fabs(sd) * I.kb2) continue;
+    I.pc_c = sd * I.kb2;
+    I.pc_beta = 1.0 / (1.0 + sd);
+    return;
+  }
+}
+
 // Matrix-vector product in the working precision: the lane-team FFT kernels
 // for FFT sizes 32/64 (forward and residual forms), the generic
 // shared-memory FFT kernels otherwise.
@@ -577,6 +631,7 @@ static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a
   } else {
     if (!p->team_only && a.mode < 2 && reg_path_ok(a.g))
       return launch_matvec_reg<R>(a, st, prof, lv.tb[sizeof(R) == 4 ? 1 : 0]);
+    if (a.pc) return cudaErrorInvalidValue;   // the preconditioned product exists only on the lane-team path
     return launch_matvec<R>(a, st, prof);
   }
 }
@@ -648,7 +703,7 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
   const int prec = sizeof(R) == 4;
   for (auto &c : w->cycles)
     if (c.B == k.B && c.m == k.m && c.adj == adj && c.force == k.force_reorth && c.prec == prec && c.D == mv.D &&
-        c.Dp == mv.Dp)
+        c.Dp == mv.Dp && c.pc == mv.pc)
       return c.exec;
   if (!p->cap_st && cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -694,7 +749,7 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
     if (graph) cudaGraphDestroy(graph);
     return nullptr;
   }
-  w->cycles.push_back({k.B, k.m, adj, k.force_reorth, prec, mv.D, mv.Dp, graph, exec});
+  w->cycles.push_back({k.B, k.m, adj, k.force_reorth, prec, mv.pc, mv.D, mv.Dp, graph, exec});
   return exec;
 }
 
@@ -750,7 +805,7 @@ static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const Mat
     cudaGraphExec_t exec = nullptr;
     for (auto &c : w->cycles)
       if (c.B == bp.B && c.m == BS_COUNT - 1 && c.adj == (int)adj && c.force == -1 && c.prec == prec &&
-          c.D == mv.D && c.Dp == mv.Dp)
+          c.D == mv.D && c.Dp == mv.Dp && c.pc == mv.pc)
         exec = c.exec;
     if (!exec) {
       if (!p->cap_st && cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -786,7 +841,7 @@ static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const Mat
           if (graph) cudaGraphDestroy(graph);
           exec = nullptr;
         } else {
-          w->cycles.push_back({bp.B, BS_COUNT - 1, (int)adj, -1, prec, mv.D, mv.Dp, graph, exec});
+          w->cycles.push_back({bp.B, BS_COUNT - 1, (int)adj, -1, prec, mv.pc, mv.D, mv.Dp, graph, exec});
         }
       }
     }
@@ -869,10 +924,15 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   double2 *h_g0 = (double2 *)grab(B * 16);
   double *h_rn = (double *)grab(B * 8);
   int *h_kc = (int *)grab(B * 4);
+  // right preconditioner (set_precond): Eq. 4 with the lane-team product,
+  // forward solves only (GSM_PRECOND_NONE in the plan turns it off)
+  const bool pc = !adj && p->d.form == GSM_FORM_E && p->d.precond == GSM_PRECOND_AUTO && !p->team_only &&
+                  reg_path_ok(g);
   for (int b = 0; b < B; ++b) {
     if ((s = make_inst(p, pts[b], g, hI[b]))) return s;
     if (rhs)
       for (int i = 0; i < 6; ++i) hI[b].a[i] = rhs[6 * b + i];
+    if (pc) set_precond(hI[b], g, lv.delta0);
   }
   cudaStream_t st = p->st;
   Profiler *prof = p->prof.on ? &p->prof : nullptr;
@@ -911,6 +971,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   mv.write_back = 1;
   mv.mode = adj ? 2 : 0;
   mv.form = p->d.form;
+  mv.pc = pc ? 1 : 0;
   mv.scale = sizeof(R) == 4 ? (const R *)k.scale32 : (const R *)k.scale64;
   MatvecArgs<double> rs;  // FP64 residual b - A x
   rs.g = g;
@@ -996,7 +1057,8 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     cudaGraphExec_t cyc = nullptr;
     if (bicg) {
       CK(bicg_cycle<R>(p, w, lv, mv, bp, V, vinst, Us, adj, prof, h_act, &cyc));
-      CK(launch_bicg_sol<R>(w->x64, g.U, V, vinst, bp, w->need, st));
+      if (pc) CK(launch_sol_update_pc<R>(k, g, w->inst, mv.iden, w->x64, g.U, V, vinst, w->need, -1, BS_D, st, prof));
+      else CK(launch_bicg_sol<R>(w->x64, g.U, V, vinst, bp, w->need, st));
       p->launches++;
     } else {
     cyc = (p->use_graphs && !prof) ? cycle_graph<R>(p, w, lv, mv, k, V, vinst, Us, adj) : nullptr;
@@ -1026,7 +1088,11 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       }
     }
     CK(launch_backsolve(k, st));
-    CK(launch_sol_update<R>(k, w->x64, g.U, V, vinst, w->need, recursive ? m : -1, st, prof));
+    if (pc)
+      CK(launch_sol_update_pc<R>(k, g, w->inst, mv.iden, w->x64, g.U, V, vinst, w->need, recursive ? m : -1, -1, st,
+                                 prof));
+    else
+      CK(launch_sol_update<R>(k, w->x64, g.U, V, vinst, w->need, recursive ? m : -1, st, prof));
     p->launches += 2;
     }
     CK(cudaMemcpyAsync(h_kc, k.kcount, B * 4, cudaMemcpyDeviceToHost, st));
@@ -1039,7 +1105,9 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       p->launches += 3;
     } else {
       // r -= A d: A d in complex64 has error ~ eps_mv ||A d|| ~ eps_mv ||r_prev||,
-      // far below tol ||b|| once a certified ||r|| <= 1e-3 ||b|| (cert_ok)
+      // far below tol ||b|| once a certified ||r|| <= 1e-3 ||b|| (cert_ok).
+      // Preconditioned: the slot holds V y and the correction is M^{-1} V y,
+      // so A d is the preconditioned product of the slot (md.pc = mv.pc).
       MatvecArgs<R> md = mv;
       md.X = V + (long long)(bicg ? (int)BS_D : m) * Us;
       md.Y = V;

@@ -49,6 +49,12 @@ struct Inst {
   double kinc[3];  // k_inc = kappa * kdir
   double kb2;      // k_b^2 = k0^2 eps_b
   double a[6];     // polarisation (complex, interleaved): E^inc_{m=0}
+  // right preconditioner M = I - s Delta_0 G(m) (Delta_0 = (Delta eps/eps_b)_0,
+  // the averaged medium): M^{-1} = alpha P_T + beta P_L per harmonic with
+  // alpha = 1 / (1 - pc_c / (k_m^2 - k_b^2)), pc_c = s Delta_0 k_b^2, and
+  // beta = 1 / (1 + s Delta_0).  pc_c = 0, pc_beta = 1 is the identity.
+  double pc_c;
+  double pc_beta;
 };
 
 // Geometry of one truncation level, passed by value to every kernel.

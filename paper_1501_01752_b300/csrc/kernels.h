@@ -88,6 +88,8 @@ template <typename R> struct MatvecArgs {
   const C *tw = nullptr;   // 256-entry twiddle table
   int mode = 0;            // 0: A x, 1: b - A x, 2: A^H x, 3: b - A^H x
   int form = 0;            // 0: Eq. 4 (E field), 1: Eq. 5 (H field; modes 0 and 1 only)
+  int pc = 0;              // 1: Y = A M^{-1} X with the right preconditioner of Inst (Eq. 4, mode 0,
+                           // lane-team path only)
   double *partial = nullptr;
   unsigned *counter = nullptr;
   double *norm_out = nullptr;  // ||Y||^2 per instance (nullptr = skip)
@@ -156,6 +158,13 @@ cudaError_t launch_backsolve(const KrylovPtrs &k, cudaStream_t st);
 template <typename R>
 cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst, typename Cx<R>::T *V,
                               long long vinst, const int *need, int dslot, cudaStream_t st, Profiler *prof);
+// right-preconditioned cycles: u = V y (GMRES, src < 0) or u = V[src]
+// (BiCGSTAB), x += M^{-1} u per harmonic (M^{-1} of Inst with the product's
+// 1/(k_m^2 - k_b^2) in the basis precision); u kept in slot dslot if >= 0
+template <typename R>
+cudaError_t launch_sol_update_pc(const KrylovPtrs &k, const Geo &g, const Inst *inst, const R *iden, double2 *x64,
+                                 long long xinst, typename Cx<R>::T *V, long long vinst, const int *need, int dslot,
+                                 int src, cudaStream_t st, Profiler *prof);
 cudaError_t launch_resid_sub(double2 *r64, long long rinst, const float2 *Ad, long long ainst, long long U, int B,
                              int nblk, const int *need, double *partial, unsigned *counter, double *norm_out,
                              cudaStream_t st);

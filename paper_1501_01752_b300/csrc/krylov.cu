@@ -320,6 +320,64 @@ __global__ void __launch_bounds__(KT) k_sol_update(double2 *__restrict__ x64, lo
   }
 }
 
+// Right-preconditioned Krylov cycles solve A M^{-1} u = r, so the
+// correction is M^{-1} u.  One thread per harmonic forms the three
+// components of u = V y (GMRES, src < 0; kept in slot dslot for
+// r -= (A M^{-1}) u when dslot >= 0) or reads them from slot src (BiCGSTAB's
+// accumulated iterate), maps them by M^{-1} = alpha P_T + beta P_L with the
+// same arithmetic as the product's pass 1, and adds the result to the FP64 x.
+template <typename R>
+__global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restrict__ inst, const R *__restrict__ iden,
+                                                      double2 *__restrict__ x64, long long xinst,
+                                                      typename Cx<R>::T *__restrict__ V, long long vinst, long long Us,
+                                                      const double2 *__restrict__ y, int m,
+                                                      const int *__restrict__ kcount, const int *__restrict__ need,
+                                                      int dslot, int src) {
+  using C = typename Cx<R>::T;
+  __shared__ C ys[MAXM];
+  const int b = blockIdx.y;
+  if (!need[b]) return;
+  const int n = src >= 0 ? 1 : kcount[b];
+  if (n == 0) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    ys[i] = src >= 0 ? mk((R)1, (R)0) : mk((R)y[(long long)b * m + i].x, (R)y[(long long)b * m + i].y);
+  __syncthreads();
+  C *Vb = V + b * vinst;
+  double2 *xb = x64 + b * xinst;
+  C *dv = dslot >= 0 ? Vb + (long long)dslot * Us : nullptr;
+  const C *V0 = Vb + (src >= 0 ? (long long)src * Us : 0);
+  const long long Nh = g.Nh;
+  const R pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < Nh; e += (long long)gridDim.x * blockDim.x) {
+    C d[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d[c] = mk((R)0, (R)0);
+    for (int i = 0; i < n; ++i) {
+      const C *Vi = V0 + (long long)i * Us + e;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) d[c] = cadd(d[c], cmul(ys[i], Vi[c * Nh]));
+    }
+    if (dv)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dv[c * Nh + e] = d[c];
+    const int row = (int)(e / g.N[0]), mx = (int)(e - (long long)row * g.N[0]);
+    const int mz = row / g.N[1], my = row - mz * g.N[1];
+    const R kx = (R)(inst[b].kinc[0] + (mx - g.n[0]) * g.K[0]);
+    const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
+    const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
+    const R al = (R)1 / ((R)1 - pcc * iden[(long long)b * Nh + e]);
+    const R k2 = kx * kx + ky * ky + kz * kz;
+    const R f = k2 > (R)0 ? (pcb - al) / k2 : (R)0;
+    const R kr = kx * d[0].x + ky * d[1].x + kz * d[2].x, ki = kx * d[0].y + ky * d[1].y + kz * d[2].y;
+    const R kc[3] = {kx, ky, kz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 xv = xb[c * Nh + e];
+      xb[c * Nh + e] = mk(xv.x + (double)(al * d[c].x + f * kc[c] * kr), xv.y + (double)(al * d[c].y + f * kc[c] * ki));
+    }
+  }
+}
+
 // r -= A d with A d from the complex64 product, and ||r||^2 (last block).
 __global__ void __launch_bounds__(KT) k_resid_sub(double2 *__restrict__ r64, long long rinst,
                                                   const float2 *__restrict__ Ad, long long ainst, long long U,
@@ -486,6 +544,24 @@ cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst
   if (prof) prof->end(KIND_OTHER, st, 0.0);
   return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t launch_sol_update_pc(const KrylovPtrs &k, const Geo &g, const Inst *inst, const R *iden, double2 *x64,
+                                 long long xinst, typename Cx<R>::T *V, long long vinst, const int *need, int dslot,
+                                 int src, cudaStream_t st, Profiler *prof) {
+  dim3 grid(k.nblk, k.B);
+  if (prof) prof->begin(KIND_OTHER, st);
+  k_sol_update_pc<R><<<grid, KT, 0, st>>>(g, inst, iden, x64, xinst, V, vinst, k.Us, k.y, k.m, k.kcount, need, dslot,
+                                          src);
+  if (prof) prof->end(KIND_OTHER, st, 0.0);
+  return cudaGetLastError();
+}
+template cudaError_t launch_sol_update_pc<float>(const KrylovPtrs &, const Geo &, const Inst *, const float *, double2 *,
+                                                 long long, float2 *, long long, const int *, int, int, cudaStream_t,
+                                                 Profiler *);
+template cudaError_t launch_sol_update_pc<double>(const KrylovPtrs &, const Geo &, const Inst *, const double *,
+                                                  double2 *, long long, double2 *, long long, const int *, int, int,
+                                                  cudaStream_t, Profiler *);
 
 cudaError_t launch_set_rhs(double2 *r64, long long xinst, const Geo &g, const Inst *inst, int B, cudaStream_t st) {
   const long long tot = (long long)B * g.U;

@@ -147,17 +147,18 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
   }
 }
 
-// Pass 1 of the H-field form (Eq. 5): the x transforms of (k_m x x), one
+// Pass 1 with a per-harmonic 3 x 3 map applied before the x transforms, one
 // team per (m_z, m_y) row holding all three components of the row, so that
-// the scaled write-back of a Krylov vector and the cross product read and
-// write only the team's own values.
+// the scaled write-back of a Krylov vector and the map read and write only
+// the team's own values.  op 0: k_m x x (H-field form, Eq. 5); op 1: M^{-1} x
+// (right preconditioner of Inst, Eq. 4; iden = 1/(k_m^2 - k_b^2)).
 template <typename R, int L0, int TT>
 __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__restrict__ X, long long xstride,
                                                   typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
                                                   int write_back, const int *__restrict__ act,
                                                   const Inst *__restrict__ inst,
                                                   const typename Cx<R>::T *__restrict__ twg, const int *__restrict__ jdev,
-                                                  long long jstride) {
+                                                  long long jstride, int op, const R *__restrict__ iden) {
   using C = typename Cx<R>::T;
   using IO = typename Io<R>::T;
   using F = Team8<L0>;
@@ -180,6 +181,8 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
   const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
   const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
   IO *Xr = X + b * xstride + r * N0;
+  const R *idr = iden ? iden + (long long)b * Nh + r * N0 : nullptr;
+  const R pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
   C v[3][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -203,6 +206,20 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
     if (write_back && valid && h >= 0)
 #pragma unroll
       for (int c = 0; c < 3; ++c) Xr[c * Nh + h] = io_out<IO>(u[c]);
+    if constexpr (!std::is_same<R, dfl>::value) {
+      if (op == 1) {
+        // M^{-1} u = alpha u + (beta - alpha) k (k . u) / k^2 (zero where no harmonic sits)
+        if (!valid || h < 0) continue;
+        const R al = (R)1 / ((R)1 - pcc * idr[h]);
+        const R k2 = kx * kx + ky * ky + kz * kz;
+        const R f = k2 > (R)0 ? (pcb - al) / k2 : (R)0;
+        const C ku = mk(kx * u[0].x + ky * u[1].x + kz * u[2].x, kx * u[0].y + ky * u[1].y + kz * u[2].y);
+        v[0][a] = mk(al * u[0].x + f * kx * ku.x, al * u[0].y + f * kx * ku.y);
+        v[1][a] = mk(al * u[1].x + f * ky * ku.x, al * u[1].y + f * ky * ku.y);
+        v[2][a] = mk(al * u[2].x + f * kz * ku.x, al * u[2].y + f * kz * ku.y);
+        continue;
+      }
+    }
     // (k x u), zero where no harmonic sits (u = 0 there)
     v[0][a] = csub(cscale(u[2], ky), cscale(u[1], kz));
     v[1][a] = csub(cscale(u[0], kz), cscale(u[2], kx));
@@ -449,7 +466,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
                                                  const int *__restrict__ act, const Inst *__restrict__ inst,
                                                  const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,
                                                  int rows, double *partial, unsigned *counter, double *norm_out,
-                                                 const int *__restrict__ jdev, long long jstride) {
+                                                 const int *__restrict__ jdev, long long jstride, int pc) {
   using C = typename Cx<R>::T;
   using IO = typename Io<R>::T;
   using F = Team8<L0>;
@@ -535,7 +552,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     }
   }
   __syncthreads();
-  const R kb2 = (R)inst[b].kb2;
+  const R kb2 = (R)inst[b].kb2, pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
   const int h0 = (g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
   IO *Yb = Y + b * ystride;
   R acc = 0;   // this thread's share of ||y||^2 (a few harmonics), widened once
@@ -549,6 +566,18 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       y1 = csub(y1, cscale(csub(cscale(u0, kz), cscale(u2, kx)), id));
       y2 = csub(y2, cscale(csub(cscale(u1, kx), cscale(u0, ky)), id));
     } else {
+      if constexpr (!std::is_same<R, dfl>::value) {
+        if (pc) {
+          // identity term of A M^{-1} x: x <- M^{-1} x = alpha x + (beta - alpha) k (k . x) / k^2
+          const R al = (R)1 / ((R)1 - pcc * id);
+          const R k2 = kx * kx + ky * ky + kz * kz;
+          const R f = k2 > (R)0 ? (pcb - al) / k2 : (R)0;
+          const R kxr = kx * y0.x + ky * y1.x + kz * y2.x, kxi = kx * y0.y + ky * y1.y + kz * y2.y;
+          y0 = mk(al * y0.x + f * kx * kxr, al * y0.y + f * kx * kxi);
+          y1 = mk(al * y1.x + f * ky * kxr, al * y1.y + f * ky * kxi);
+          y2 = mk(al * y2.x + f * kz * kxr, al * y2.y + f * kz * kxi);
+        }
+      }
       const R kux = kx * u0.x + ky * u1.x + kz * u2.x, kuy = kx * u0.y + ky * u1.y + kz * u2.y;
       y0.x -= id * (kb2 * u0.x - kx * kux);
       y0.y -= id * (kb2 * u0.y - kx * kuy);
@@ -612,10 +641,10 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
   const Geo &g = a.g;
   if (g.L[0] == 128) {
     constexpr int TX = tt128<R, TT>();
-    if (a.form) {
+    if (a.form || a.pc) {
       dim3 gridh((int)(((long long)g.N[2] * g.N[1] + TX / 16 - 1) / (TX / 16)), a.B);
       k_fwd_x_t8h<R, 128, TX><<<gridh, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
-                                                    a.tw, a.jdev, a.jstride);
+                                                    a.tw, a.jdev, a.jstride, a.form ? 0 : 1, a.iden);
     } else {
       const int RB = TX / 16 * P1_RPT;
       dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
@@ -626,15 +655,16 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
   }
   const int RB = TT / (g.L[0] / 8) * P1_RPT;
   dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
-  if (a.form) {
+  if (a.form || a.pc) {
     const int RBH = TT / (g.L[0] / 8);
+    const int op = a.form ? 0 : 1;
     dim3 gridh((int)(((long long)g.N[2] * g.N[1] + RBH - 1) / RBH), a.B);
     if (g.L[0] == 64)
       k_fwd_x_t8h<R, 64, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
-                                                   a.tw, a.jdev, a.jstride);
+                                                   a.tw, a.jdev, a.jstride, op, a.iden);
     else
       k_fwd_x_t8h<R, 32, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
-                                                   a.tw, a.jdev, a.jstride);
+                                                   a.tw, a.jdev, a.jstride, op, a.iden);
     return;
   }
   if (g.L[0] == 64)
@@ -689,7 +719,7 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   cudaFuncSetAttribute(k_inv_x_t8<R, 128, M, TX, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
   k_inv_x_t8<R, 128, M, TX, HF><<<grid, TX, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,   \
                                                         a.iden, a.tw, rows, a.partial, a.counter, a.norm_out,     \
-                                                        a.jdev, a.jstride)
+                                                        a.jdev, a.jstride, a.pc)
     if (a.form) { if (a.mode == 1) { GSM_P3X(1, 1); } else { GSM_P3X(0, 1); } }
     else { if (a.mode == 1) { GSM_P3X(1, 0); } else { GSM_P3X(0, 0); } }
 #undef GSM_P3X
@@ -702,7 +732,7 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   cudaFuncSetAttribute(k_inv_x_t8<R, L0, M, TT, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
   k_inv_x_t8<R, L0, M, TT, HF><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,     \
                                                        a.iden, a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, \
-                                                       a.jstride)
+                                                       a.jstride, a.pc)
   if (g.L[0] == 64) {
     if (a.form) { if (a.mode == 1) { GSM_P3(64, 1, 1); } else { GSM_P3(64, 0, 1); } }
     else { if (a.mode == 1) { GSM_P3(64, 1, 0); } else { GSM_P3(64, 0, 0); } }
@@ -728,12 +758,28 @@ template <typename R, int TT> struct P1 { static void run(const MatvecArgs<R> &a
 template <typename R, int TT> struct P2 { static void run(const MatvecArgs<R> &a, cudaStream_t st) { pass2<R, TT>(a, st); } };
 template <typename R, int TT> struct P3 { static void run(const MatvecArgs<R> &a, cudaStream_t st) { pass3<R, TT>(a, st); } };
 
+// One pass of the lane-team product with a given block size.  Each
+// (precision, pass) pair is instantiated in a translation unit of its own
+// (matvec_reg_<precision>_p<pass>.cu), so that the passes compile in
+// parallel; the units that instantiate launch_reg_pass declare them extern.
+template <typename R, int PASS>
+cudaError_t reg_pass(int tb, const MatvecArgs<R> &a, cudaStream_t st) {
+  if constexpr (PASS == 1) return dispatch_tb<R, P1>(tb, a, st);
+  else if constexpr (PASS == 2) return dispatch_tb<R, P2>(tb, a, st);
+  else return dispatch_tb<R, P3>(tb, a, st);
+}
+
+#define GSM_EXTERN_REG_PASSES(R)                                                          \
+  extern template cudaError_t reg_pass<R, 1>(int, const MatvecArgs<R> &, cudaStream_t);  \
+  extern template cudaError_t reg_pass<R, 2>(int, const MatvecArgs<R> &, cudaStream_t);  \
+  extern template cudaError_t reg_pass<R, 3>(int, const MatvecArgs<R> &, cudaStream_t);
+
 // One pass of the lane-team product with a given block size (autotuner).
 template <typename R>
 cudaError_t launch_reg_pass(int pass, int tb, const MatvecArgs<R> &a, cudaStream_t st) {
-  if (pass == 1) return dispatch_tb<R, P1>(tb, a, st);
-  if (pass == 2) return dispatch_tb<R, P2>(tb, a, st);
-  return dispatch_tb<R, P3>(tb, a, st);
+  if (pass == 1) return reg_pass<R, 1>(tb, a, st);
+  if (pass == 2) return reg_pass<R, 2>(tb, a, st);
+  return reg_pass<R, 3>(tb, a, st);
 }
 
 template <typename R>

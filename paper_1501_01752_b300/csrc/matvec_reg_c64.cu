@@ -4,6 +4,8 @@
 
 namespace gsm {
 
+GSM_EXTERN_REG_PASSES(float)
+
 // Dp[r_x / 2][r_y][r_z] = (D[r_x][r_y][r_z], D[r_x + 1][r_y][r_z])
 __global__ void k_pair_d(const float *__restrict__ D, float2 *__restrict__ Dp, long long plane, long long npairs) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs * plane;

@@ -4,6 +4,8 @@
 
 namespace gsm {
 
+GSM_EXTERN_REG_PASSES(dfl)
+
 template cudaError_t launch_matvec_reg<dfl>(const MatvecArgs<dfl> &, cudaStream_t, Profiler *, const int *);
 
 }  // namespace gsm

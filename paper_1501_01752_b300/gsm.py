@@ -25,6 +25,7 @@ DF64 = 2                      # gsm_apply only: the double-float product (outer-
 RESID_AUTO, RESID_FP64 = 0, 1
 FORM_E, FORM_H = 0, 1         # Eq. 4 (E field) or Eq. 5 (H field)
 GMRES, BICGSTAB = 0, 1
+PRECOND_AUTO, PRECOND_NONE = 0, 1   # averaged-medium right preconditioner of GMRES on Eq. 4, or none
 KIND_FWD_X, KIND_YZ, KIND_INV_X, KIND_DOTS, KIND_UPDATE, KIND_OTHER, KIND_RESID64, KIND_LAUNCHES = range(8)
 
 
@@ -40,7 +41,7 @@ class PlanDesc(ct.Structure):
                 ("restart", ct.c_int), ("max_iter", ct.c_int), ("tol", ct.c_double),
                 ("inner_tol", ct.c_double), ("max_batch", ct.c_int), ("hbm_cap_bytes", ct.c_size_t),
                 ("device", ct.c_int), ("cuda_stream", ct.c_void_p), ("residual", ct.c_int),
-                ("form", ct.c_int)]
+                ("form", ct.c_int), ("precond", ct.c_int)]
 
 
 class Shape(ct.Structure):
@@ -136,7 +137,7 @@ def plan_query(periods, n_harm, precision=FP32_REFINE, fft=(0, 0, 0), max_batch=
 
 
 def _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, max_batch, hbm_cap, device,
-          stream, fft, residual=RESID_AUTO, krylov=GMRES, form=FORM_E):
+          stream, fft, residual=RESID_AUTO, krylov=GMRES, form=FORM_E, precond=PRECOND_AUTO):
     d = PlanDesc()
     for a in range(3):
         d.period[a] = periods[a]
@@ -156,6 +157,7 @@ def _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, 
     d.cuda_stream = stream
     d.residual = residual
     d.form = form
+    d.precond = precond
     return d
 
 
@@ -164,13 +166,13 @@ class Plan:
 
     def __init__(self, periods, n_harm, eps_b=1.0, precision=FP32_REFINE, restart=0, max_iter=0, tol=0.0,
                  inner_tol=0.0, max_batch=0, hbm_cap=0, device=0, stream=None, fft=(0, 0, 0), residual=RESID_AUTO,
-                 krylov=GMRES, form=FORM_E):
+                 krylov=GMRES, form=FORM_E, precond=PRECOND_AUTO):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
         self.n_harm = tuple(n_harm)
         self.desc = _desc(periods, n_harm, eps_b, precision, restart, max_iter, tol, inner_tol, max_batch,
-                          hbm_cap, device, stream, fft, residual, krylov, form)
+                          hbm_cap, device, stream, fft, residual, krylov, form, precond)
         h = ct.c_void_p()
         s = lib.gsm_plan(ct.byref(self.desc), ct.byref(h))
         if s:

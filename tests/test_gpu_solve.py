@@ -181,10 +181,13 @@ def test_singular_harmonic_anywhere_in_the_box():
 
 
 @pytest.mark.parametrize("krylov", ["gmres", "bicgstab"])
-def test_new_permittivity_rebuilds_captured_cycles(krylov):
+def test_new_permittivity_rebuilds_captured_cycles(krylov, monkeypatch):
     # captured inner cycles hold the multiplier's device address; after
     # gsm_set_permittivity the same plan must solve the new structure exactly
-    # like a fresh plan (and never read the freed multiplier)
+    # like a fresh plan (and never read the freed multiplier).  Block sizes
+    # are fixed: the autotuner times each plan's first batch, and another
+    # choice changes the summation order of the norms (and so the last bits)
+    monkeypatch.setenv("GSM_BLOCKS", "256,256,256")
     g = gsm()
     n_harm = (15, 15, 15)
     pts = wl.woodpile_batch(4)
