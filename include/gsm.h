@@ -68,9 +68,10 @@ enum { GSM_RESID_AUTO = 0, GSM_RESID_FP64 = 1 };
  * incident H amplitude and the output field is H) */
 enum { GSM_FORM_E = 0, GSM_FORM_H = 1 };
 enum { GSM_GMRES = 0, GSM_BICGSTAB = 1 };            /* Krylov method            */
-/* GMRES on Eq. 4 with the lane-team product (FFT sizes 32/64, cubic 128):
- * right preconditioner M = I - s Delta_0 G(m), the block diagonal of Eq. 4
- * (the Green tensor of the cell-averaged medium, inverted in closed form per
+/* Krylov solves of Eq. 4 with the lane-team product (FFT sizes 32/64, cubic
+ * 128) and a contrast |Delta_0| = |<eps>/eps_b - 1| >= 1: right
+ * preconditioner M = I - s Delta_0 G(m), the block diagonal of Eq. 4 (the
+ * Green tensor of the cell-averaged medium, inverted in closed form per
  * harmonic; s in {1, 1/2, 1/4, 1/8} per point keeps M away from singular,
  * s = 0 when no choice does), or none.  The solution is the same; only the
  * number of Krylov steps changes.  Not in the paper. */

@@ -42,6 +42,10 @@ def _window(k0, n, lo=0.85, hi=1.15):
     return max(n * lo, 1.03) * k0, n * hi * k0
 
 
+def _pc(args):
+    return gsm.PRECOND_NONE if getattr(args, "precond", "auto") == "none" else gsm.PRECOND_AUTO
+
+
 def run(name, args):
     torch.cuda.init()
     {"matvec": matvec, "sweep": sweep, "gyroid": gyroid, "adjoint": adjoint, "optimise": optimise}[name](args)
@@ -101,7 +105,7 @@ def sweep(args):
     st = wl.ellipsoid_lattice(period=1.0)
     f = 4 * math.pi / 3 * 0.4 * 0.3 * 0.2
     n_mg = math.sqrt(_mg(6.0, 1.0, f))
-    plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=64)
+    plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=64, precond=_pc(args))
     pts, groups = [], []
     for gi in range(16):
         ratio = 0.10 + 0.02 * gi
@@ -134,7 +138,7 @@ def sweep(args):
     iters = [i["iters"] for i in infos]
     print(json.dumps({
         "workload": "sweep: ellipsoid lattice eps 6, 16 omega x 16 kappa x 2 pol, N = 15/21/31",
-        "solves": len(pts), "seconds": t_sweep, "solves_per_s": len(pts) / t_sweep,
+        "precond": getattr(args, "precond", "auto"), "solves": len(pts), "seconds": t_sweep, "solves_per_s": len(pts) / t_sweep,
         "retrieval_host_ms": 1000 * t_fit, "iters_mean": float(np.mean(iters)),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "eps_xx_by_ratio": out[0::2], "eps_yy_by_ratio": out[1::2], "n_MG": n_mg}), flush=True)
@@ -156,11 +160,12 @@ def gyroid(args):
     coarse.close()
     pt = wl.point(eta * (1 + 1e-3), (0, 0, 1), (1, 0, 0), k0)
     res = {"workload": "gyroid g > 0.5 eps 12, Lambda 0.4, 63^3 harmonics, 128^3 grid, 256 MB Krylov cap",
-           "fill": f, "kappa_over_k0": pt["kappa"] / k0, "eta15_over_k0": eta / k0}
+           "fill": f, "kappa_over_k0": pt["kappa"] / k0, "eta15_over_k0": eta / k0,
+           "precond": getattr(args, "precond", "auto")}
     U = 3 * 63 ** 3
     for name, prec in (("c64_refine", gsm.FP32_REFINE), ("fp64", gsm.FP64)):
         plan = gsm.plan_for(st, (63, 63, 63), precision=prec, tol=1e-8, max_batch=1, hbm_cap=256 << 20,
-                            max_iter=20000)
+                            max_iter=20000, precond=_pc(args))
         E = torch.empty(U, dtype=torch.complex128, device="cuda")
         t = []
         for _ in range(2):   # the first solve also loads kernels, tunes block sizes and captures graphs

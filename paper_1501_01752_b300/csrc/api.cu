@@ -602,11 +602,13 @@ static double min_gap(const Inst &I, const Geo &g, double T) {
 // light cone of the averaged medium, so s is the largest of 1, 1/2, 1/4, 1/8
 // that keeps every |k_m^2 - k_b^2 (1 + s Delta_0)| >= 0.1 s |Delta_0| k_b^2
 // (|alpha - 1| <= 10) and 1 + s Delta_0 >= 0.1; 0 (no preconditioner) if
-// none does.
+// none does.  Weak contrasts (|Delta_0| < 1, the averaged medium less than
+// twice eps_b) get none: measured on the ellipsoid sweep (Delta_0 = 0.5) it
+// saved no Krylov steps and cost the extra work of the three-component pass 1.
 static void set_precond(Inst &I, const Geo &g, double d0) {
   I.pc_c = 0.0;
   I.pc_beta = 1.0;
-  if (!(std::fabs(d0) > 0) || !std::isfinite(d0)) return;
+  if (!(std::fabs(d0) >= 1.0) || !std::isfinite(d0)) return;
   for (double s = 1.0; s >= 0.125; s *= 0.5) {
     const double sd = s * d0;
     if (1.0 + sd < 0.1) continue;
@@ -927,7 +929,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   // right preconditioner (set_precond): Eq. 4 with the lane-team product,
   // forward solves only (GSM_PRECOND_NONE in the plan turns it off)
   const bool pc = !adj && p->d.form == GSM_FORM_E && p->d.precond == GSM_PRECOND_AUTO && !p->team_only &&
-                  reg_path_ok(g);
+                  reg_path_ok(g) && std::fabs(lv.delta0) >= 1.0;
   for (int b = 0; b < B; ++b) {
     if ((s = make_inst(p, pts[b], g, hI[b]))) return s;
     if (rhs)
