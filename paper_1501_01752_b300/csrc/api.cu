@@ -747,7 +747,10 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
   }
   ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
   if (!ok) {
-    cudaGetLastError();
+    // the caller falls back to step-by-step launches; GSM_DEBUG=1 says why
+    const cudaError_t why = cudaGetLastError();
+    if (const char *dbg = std::getenv("GSM_DEBUG"))
+      if (dbg[0] == '1') std::fprintf(stderr, "gsm: inner-cycle graph not captured (%s)\n", cudaGetErrorString(why));
     if (graph) cudaGraphDestroy(graph);
     return nullptr;
   }

@@ -40,6 +40,48 @@ __device__ __forceinline__ double2 shfl_xor1(double2 v, unsigned mask) {
   return make_double2(__shfl_xor_sync(mask, v.x, 1), __shfl_xor_sync(mask, v.y, 1));
 }
 
+// reciprocal in the working precision (the preconditioner's alpha and 1/k^2:
+// FP32 through the correctly rounded reciprocal intrinsic, cheaper than a
+// division; every kernel that applies M^{-1} uses the same call)
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+// packed FP32 pair arithmetic of sm_100+ (one add/sub/mul/fma .f32x2
+// instruction per call, both lanes rounded to nearest)
+namespace f2 {
+__device__ __forceinline__ unsigned long long u(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 f(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 add(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(u(a)), "l"(u(b)));
+  return f(d);
+}
+__device__ __forceinline__ float2 sub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(u(a)), "l"(u(b)));
+  return f(d);
+}
+__device__ __forceinline__ float2 mul(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(u(a)), "l"(u(b)));
+  return f(d);
+}
+// a * b + c
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(u(a)), "l"(u(b)), "l"(u(c)));
+  return f(d);
+}
+}  // namespace f2
+
 // read-only loads of twiddle-table entries
 __device__ __forceinline__ float2 ldg_c(const float2 *p) { return __ldg(p); }
 __device__ __forceinline__ double2 ldg_c(const double2 *p) { return __ldg(p); }

@@ -84,6 +84,89 @@ __device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
 __device__ __forceinline__ dfl &operator-=(dfl &a, dfl b) { return a = a - b; }
 __device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = a * b; }
 
+// Complex double-float addition, subtraction and products with the packed
+// FP32 instructions of sm_100+ (common.cuh, namespace f2): the real part in
+// lane 0 and the imaginary part in lane 1 of every pair go through the same
+// error-free steps as the scalar operators above, in the same order, so the
+// results are bit-identical to the scalar code with half the instructions.
+// These overloads take precedence over the generic complex templates of
+// common.cuh wherever the complex type is dcx.
+namespace dpk {
+struct P {
+  float2 hi, lo;   // (re.hi, im.hi), (re.lo, im.lo)
+};
+__device__ __forceinline__ P pk(dcx a) { return {make_float2(a.x.hi, a.y.hi), make_float2(a.x.lo, a.y.lo)}; }
+__device__ __forceinline__ dcx un(P p) { return mk(dfl(p.hi.x, p.lo.x), dfl(p.hi.y, p.lo.y)); }
+__device__ __forceinline__ P fast_two_sum(float2 a, float2 b) {
+  const float2 s = f2::add(a, b);
+  return {s, f2::sub(b, f2::sub(s, a))};
+}
+// (a.hi + b.hi) error-free, then the low parts: the scalar operator+
+__device__ __forceinline__ P add(P a, P b) {
+  const float2 s = f2::add(a.hi, b.hi);
+  const float2 bb = f2::sub(s, a.hi);
+  const float2 e = f2::add(f2::sub(a.hi, f2::sub(s, bb)), f2::sub(b.hi, bb));
+  return fast_two_sum(s, f2::add(e, f2::add(a.lo, b.lo)));
+}
+// a + (-b) of the scalar operators, written with subtractions: x + (-y) and
+// x - y round identically, and so do (-y) - z and -(y + z)
+__device__ __forceinline__ P sub(P a, P b) {
+  const float2 s = f2::sub(a.hi, b.hi);
+  const float2 bb = f2::sub(s, a.hi);
+  const float2 e = f2::sub(f2::sub(a.hi, f2::sub(s, bb)), f2::add(b.hi, bb));
+  return fast_two_sum(s, f2::add(e, f2::sub(a.lo, b.lo)));
+}
+// lane-wise double-float products (the scalar operator*)
+__device__ __forceinline__ P mul(P a, P b) {
+  const float2 p = f2::mul(a.hi, b.hi);
+  float2 e = f2::fma(a.hi, b.hi, f2::mul(p, make_float2(-1.f, -1.f)));
+  e = f2::fma(a.hi, b.lo, e);
+  e = f2::fma(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+}  // namespace dpk
+
+__device__ __forceinline__ dcx cadd(dcx a, dcx b) { return dpk::un(dpk::add(dpk::pk(a), dpk::pk(b))); }
+__device__ __forceinline__ dcx csub(dcx a, dcx b) { return dpk::un(dpk::sub(dpk::pk(a), dpk::pk(b))); }
+// (a.x b.x - a.y b.y, a.x b.y + a.y b.x): both products of each part in one
+// packed product, the real part's second product negated (exact) before the
+// packed sum, as the scalar t1 + (-t2)
+__device__ __forceinline__ dcx cmul(dcx a, dcx b) {
+  const dpk::P ax = {make_float2(a.x.hi, a.x.hi), make_float2(a.x.lo, a.x.lo)};
+  const dpk::P ay = {make_float2(a.y.hi, a.y.hi), make_float2(a.y.lo, a.y.lo)};
+  const dpk::P bxy = dpk::pk(b);
+  const dpk::P byx = {make_float2(b.y.hi, b.x.hi), make_float2(b.y.lo, b.x.lo)};
+  const dpk::P t13 = dpk::mul(ax, bxy);
+  dpk::P t24 = dpk::mul(ay, byx);
+  const float2 sg = make_float2(-1.f, 1.f);
+  t24.hi = f2::mul(t24.hi, sg);
+  t24.lo = f2::mul(t24.lo, sg);
+  return dpk::un(dpk::add(t13, t24));
+}
+// (a.x s, a.y s)
+__device__ __forceinline__ dcx cscale(dcx a, dfl s) {
+  const dpk::P ss = {make_float2(s.hi, s.hi), make_float2(s.lo, s.lo)};
+  return dpk::un(dpk::mul(dpk::pk(a), ss));
+}
+
+// the radix-8 rotations (fft.cuh) for dcx: the same sums and products as
+// the generic versions, both parts in one packed pass
+template <int S> __device__ __forceinline__ dcx rot8(dcx a) {
+  const dfl h(0.70710678118654752440);
+  const dpk::P sw = S > 0 ? dpk::P{make_float2(-a.y.hi, a.x.hi), make_float2(-a.y.lo, a.x.lo)}
+                          : dpk::P{make_float2(a.y.hi, -a.x.hi), make_float2(a.y.lo, -a.x.lo)};
+  const dpk::P hh = {make_float2(h.hi, h.hi), make_float2(h.lo, h.lo)};
+  return dpk::un(dpk::mul(dpk::add(dpk::pk(a), sw), hh));
+}
+template <int S> __device__ __forceinline__ dcx rot8_3(dcx a) {
+  const dfl h(0.70710678118654752440);
+  const dpk::P na = {make_float2(-a.x.hi, -a.y.hi), make_float2(-a.x.lo, -a.y.lo)};
+  const dpk::P sw = S > 0 ? dpk::P{make_float2(-a.y.hi, a.x.hi), make_float2(-a.y.lo, a.x.lo)}
+                          : dpk::P{make_float2(a.y.hi, -a.x.hi), make_float2(a.y.lo, -a.x.lo)};
+  const dpk::P hh = {make_float2(h.hi, h.hi), make_float2(h.lo, h.lo)};
+  return dpk::un(dpk::mul(dpk::add(na, sw), hh));
+}
+
 __device__ __forceinline__ dcx shfl_xor1(dcx v, unsigned mask) {
   return mk(dfl(__shfl_xor_sync(mask, v.x.hi, 1), __shfl_xor_sync(mask, v.x.lo, 1)),
             dfl(__shfl_xor_sync(mask, v.y.hi, 1), __shfl_xor_sync(mask, v.y.lo, 1)));

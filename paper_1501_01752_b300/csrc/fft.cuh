@@ -30,6 +30,19 @@ template <int S, typename C> __device__ __forceinline__ C mul_si(C a) {  // a * 
   return S > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
 }
 
+// The w_8 and w_8^3 rotations of the radix-8 DFT: (1 + S i) h a and
+// (-1 + S i) h a with h = 1/sqrt(2) (dfloat.cuh has packed versions for dcx)
+template <int S, typename C> __device__ __forceinline__ C rot8(C a) {
+  using R = decltype(a.x);
+  const R h = (R)0.70710678118654752440;
+  return mk((a.x - S * a.y) * h, (a.y + S * a.x) * h);
+}
+template <int S, typename C> __device__ __forceinline__ C rot8_3(C a) {
+  using R = decltype(a.x);
+  const R h = (R)0.70710678118654752440;
+  return mk((-a.x - S * a.y) * h, (-a.y + S * a.x) * h);
+}
+
 template <int S, typename C> __device__ __forceinline__ void dft2(C* v) {
   C t = v[0];
   v[0] = cadd(t, v[1]);
@@ -51,12 +64,10 @@ template <int S, typename C> __device__ __forceinline__ void dft8(C* v) {
   C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
   dft4<S>(e0, e1, e2, e3);
   dft4<S>(o0, o1, o2, o3);
-  using R = decltype(o0.x);
-  const R h = (R)0.70710678118654752440;
   // w = exp(S i pi / 4): w o1 = (1 + S i) h o1, w^2 o2 = S i o2, w^3 o3 = (-1 + S i) h o3
-  C t1 = mk((o1.x - S * o1.y) * h, (o1.y + S * o1.x) * h);
+  C t1 = rot8<S>(o1);
   C t2 = mul_si<S>(o2);
-  C t3 = mk((-o3.x - S * o3.y) * h, (-o3.y + S * o3.x) * h);
+  C t3 = rot8_3<S>(o3);
   v[0] = cadd(e0, o0);
   v[4] = csub(e0, o0);
   v[1] = cadd(e1, t1);

@@ -95,11 +95,9 @@ template <int L> struct Team8 {
     const C o0 = cadd(v[1], v[7]), o2 = csub(v[1], v[7]);
     const C r7 = mul_si<S>(v[7]);
     const C o1 = csub(v[1], r7), o3 = cadd(v[1], r7);
-    using R = decltype(o0.x);
-    const R h = (R)0.70710678118654752440;
-    const C t1 = mk((o1.x - S * o1.y) * h, (o1.y + S * o1.x) * h);
+    const C t1 = rot8<S>(o1);
     const C t2 = mul_si<S>(o2);
-    const C t3 = mk((-o3.x - S * o3.y) * h, (-o3.y + S * o3.x) * h);
+    const C t3 = rot8_3<S>(o3);
     v[0] = cadd(e0, o0);
     v[4] = csub(e0, o0);
     v[1] = cadd(e1, t1);

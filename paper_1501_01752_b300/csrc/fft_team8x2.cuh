@@ -25,40 +25,6 @@ struct CP {
   float2 re, im;
 };
 
-// packed FP32 pair arithmetic (one instruction per call)
-namespace f2 {
-__device__ __forceinline__ unsigned long long u(float2 a) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
-  return r;
-}
-__device__ __forceinline__ float2 f(unsigned long long r) {
-  float2 a;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
-  return a;
-}
-__device__ __forceinline__ float2 add(float2 a, float2 b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(u(a)), "l"(u(b)));
-  return f(d);
-}
-__device__ __forceinline__ float2 sub(float2 a, float2 b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(u(a)), "l"(u(b)));
-  return f(d);
-}
-__device__ __forceinline__ float2 mul(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(u(a)), "l"(u(b)));
-  return f(d);
-}
-// a * b + c
-__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(u(a)), "l"(u(b)), "l"(u(c)));
-  return f(d);
-}
-}  // namespace f2
 
 __device__ __forceinline__ CP cp_add(CP a, CP b) { return {f2::add(a.re, b.re), f2::add(a.im, b.im)}; }
 __device__ __forceinline__ CP cp_sub(CP a, CP b) { return {f2::sub(a.re, b.re), f2::sub(a.im, b.im)}; }

@@ -352,7 +352,19 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
     C d[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) d[c] = mk((R)0, (R)0);
-    for (int i = 0; i < n; ++i) {
+    int i = 0;
+    for (; i + 4 <= n; i += 4) {       // twelve independent loads in flight
+      C vv[4][3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vv[u][c] = V0[(long long)(i + u) * Us + c * Nh + e];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[c] = cadd(d[c], cmul(ys[i + u], vv[u][c]));
+    }
+    for (; i < n; ++i) {
       const C *Vi = V0 + (long long)i * Us + e;
 #pragma unroll
       for (int c = 0; c < 3; ++c) d[c] = cadd(d[c], cmul(ys[i], Vi[c * Nh]));
@@ -365,9 +377,9 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
     const R kx = (R)(inst[b].kinc[0] + (mx - g.n[0]) * g.K[0]);
     const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
     const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
-    const R al = (R)1 / ((R)1 - pcc * iden[(long long)b * Nh + e]);
+    const R al = rcp((R)1 - pcc * iden[(long long)b * Nh + e]);
     const R k2 = kx * kx + ky * ky + kz * kz;
-    const R f = k2 > (R)0 ? (pcb - al) / k2 : (R)0;
+    const R f = k2 > (R)0 ? (pcb - al) * rcp(k2) : (R)0;
     const R kr = kx * d[0].x + ky * d[1].x + kz * d[2].x, ki = kx * d[0].y + ky * d[1].y + kz * d[2].y;
     const R kc[3] = {kx, ky, kz};
 #pragma unroll

@@ -210,9 +210,9 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
       if (op == 1) {
         // M^{-1} u = alpha u + (beta - alpha) k (k . u) / k^2 (zero where no harmonic sits)
         if (!valid || h < 0) continue;
-        const R al = (R)1 / ((R)1 - pcc * idr[h]);
+        const R al = rcp((R)1 - pcc * idr[h]);
         const R k2 = kx * kx + ky * ky + kz * kz;
-        const R f = k2 > (R)0 ? (pcb - al) / k2 : (R)0;
+        const R f = k2 > (R)0 ? (pcb - al) * rcp(k2) : (R)0;
         const C ku = mk(kx * u[0].x + ky * u[1].x + kz * u[2].x, kx * u[0].y + ky * u[1].y + kz * u[2].y);
         v[0][a] = mk(al * u[0].x + f * kx * ku.x, al * u[0].y + f * kx * ku.y);
         v[1][a] = mk(al * u[1].x + f * ky * ku.x, al * u[1].y + f * ky * ku.y);
@@ -301,9 +301,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
         const R *Dc = Dx + (long long)ry * LZ;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const R d = Dc[FZ::freq(ln.lane, q)];
-          v[q].x *= d;
-          v[q].y *= d;
+          v[q] = cscale(v[q], Dc[FZ::freq(ln.lane, q)]);
         }
       }
       FZ::template inverse<-1>(v, ln.lane, w, bf, ln.mask);
@@ -569,9 +567,9 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       if constexpr (!std::is_same<R, dfl>::value) {
         if (pc) {
           // identity term of A M^{-1} x: x <- M^{-1} x = alpha x + (beta - alpha) k (k . x) / k^2
-          const R al = (R)1 / ((R)1 - pcc * id);
+          const R al = rcp((R)1 - pcc * id);
           const R k2 = kx * kx + ky * ky + kz * kz;
-          const R f = k2 > (R)0 ? (pcb - al) / k2 : (R)0;
+          const R f = k2 > (R)0 ? (pcb - al) * rcp(k2) : (R)0;
           const R kxr = kx * y0.x + ky * y1.x + kz * y2.x, kxi = kx * y0.y + ky * y1.y + kz * y2.y;
           y0 = mk(al * y0.x + f * kx * kxr, al * y0.y + f * kx * kxi);
           y1 = mk(al * y1.x + f * ky * kxr, al * y1.y + f * ky * kxi);
