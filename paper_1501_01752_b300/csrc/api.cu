@@ -530,54 +530,29 @@ static gsm_status point_level(gsm_plan_t *p, const gsm_point &pt, int N[3]) {
   return GSM_OK;
 }
 
-static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, Inst &I) {
-  const double nrm = std::sqrt(pt.kdir[0] * pt.kdir[0] + pt.kdir[1] * pt.kdir[1] + pt.kdir[2] * pt.kdir[2]);
-  if (!(nrm > 0) || !(pt.k0 > 0) || !std::isfinite(pt.kappa)) return fail(p, GSM_ERR_ARG, "bad point (k0, kdir, kappa)");
-  for (int a = 0; a < 3; ++a) I.kinc[a] = pt.kappa * pt.kdir[a] / nrm;
-  I.kb2 = pt.k0 * pt.k0 * p->d.eps_b[0];
-  for (int i = 0; i < 6; ++i) I.a[i] = pt.pol[i];
-  I.pc_c = 0.0;     // preconditioner off (identity) unless the solve sets it
-  I.pc_beta = 1.0;
-  // Eq. 4 needs k_m^2 != k_b^2 for every harmonic (text after Eq. 4).  Along
-  // each (m_y, m_z) row, k_m^2 - k_b^2 = (kx0 + m_x K_x)^2 - (k_b^2 - c) is a
-  // parabola in m_x, closest to zero at the one or two m_x nearest the roots
-  // kx = +-sqrt(k_b^2 - c) (or at the vertex when k_b^2 < c): only those are
-  // tested, an O(N^2) scan instead of O(N^3).
-  const double tol = 1e-9 * I.kb2;
-  for (int mz = -g.n[2]; mz <= g.n[2]; ++mz)
-    for (int my = -g.n[1]; my <= g.n[1]; ++my) {
-      const double ky = I.kinc[1] + my * g.K[1], kz = I.kinc[2] + mz * g.K[2];
-      const double c = ky * ky + kz * kz, r2 = I.kb2 - c;
-      double targets[2] = {0.0, 0.0};
-      int nt = 1;
-      if (r2 > 0) {
-        targets[0] = std::sqrt(r2);
-        targets[1] = -targets[0];
-        nt = 2;
-      }
-      for (int t = 0; t < nt; ++t) {
-        const double mc = (targets[t] - I.kinc[0]) / g.K[0];
-        const int m0 = (int)std::floor(mc);
-        for (int mx = m0 - 1; mx <= m0 + 2; ++mx) {
-          if (mx < -g.n[0] || mx > g.n[0]) continue;
-          const double kx = I.kinc[0] + mx * g.K[0];
-          if (std::fabs(kx * kx + c - I.kb2) <= tol)
-            return fail(p, GSM_ERR_SINGULAR, "harmonic on the basis light cone (k_m^2 = k_b^2); shift kappa or eps_b");
-        }
-      }
-    }
-  return GSM_OK;
-}
-
-// Smallest |k_m^2 - T| over the harmonic box.  Along each (m_y, m_z) row,
-// k_m^2 - T = (kx0 + m_x K_x)^2 - (T - c) is a parabola in m_x, so only the
-// m_x nearest its roots (or its vertex) can be closest; they are clamped
-// to the box, where the parabola is monotone beyond them.
-static double min_gap(const Inst &I, const Geo &g, double T) {
-  double best = INFINITY;
-  for (int mz = -g.n[2]; mz <= g.n[2]; ++mz)
-    for (int my = -g.n[1]; my <= g.n[1]; ++my) {
-      const double ky = I.kinc[1] + my * g.K[1], kz = I.kinc[2] + mz * g.K[2];
+// Smallest |k_m^2 - T| over the harmonic box, or cut when no harmonic comes
+// closer than cut (cut > 0).  Only rows (m_y, m_z) with k_y^2 + k_z^2 < T + cut
+// can: for the others k_m^2 - T >= k_y^2 + k_z^2 - T >= cut.  Those rows lie
+// in a disk of the (k_y, k_z) plane whose index ranges follow from the radius
+// (widened by one index against rounding).  Along a row, k_m^2 - T =
+// (kx0 + m_x K_x)^2 - (T - c) is a parabola in m_x, so only the m_x nearest
+// its roots (or its vertex) can be closest; they are clamped to the box, where
+// the parabola is monotone beyond them.  O(rows in the disk), a handful for
+// the usual T ~ k0^2 << K^2, instead of O(N^2) rows per point.
+static double min_gap(const Inst &I, const Geo &g, double T, double cut) {
+  double best = cut;
+  auto span = [](double k0, double K, int n, double R, int &lo, int &hi) {
+    lo = std::max(-n, (int)std::floor((-R - k0) / K) - 1);
+    hi = std::min(n, (int)std::ceil((R - k0) / K) + 1);
+  };
+  int z0, z1;
+  span(I.kinc[2], g.K[2], g.n[2], std::sqrt(std::max(T + cut, 0.0)), z0, z1);
+  for (int mz = z0; mz <= z1; ++mz) {
+    const double kz = I.kinc[2] + mz * g.K[2];
+    int y0, y1;
+    span(I.kinc[1], g.K[1], g.n[1], std::sqrt(std::max(T + cut - kz * kz, 0.0)), y0, y1);
+    for (int my = y0; my <= y1; ++my) {
+      const double ky = I.kinc[1] + my * g.K[1];
       const double c = ky * ky + kz * kz, r2 = T - c;
       const double targets[2] = {r2 > 0 ? std::sqrt(r2) : 0.0, r2 > 0 ? -std::sqrt(r2) : 0.0};
       for (int t = 0; t < 2; ++t) {
@@ -589,7 +564,23 @@ static double min_gap(const Inst &I, const Geo &g, double T) {
         }
       }
     }
+  }
   return best;
+}
+
+static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, Inst &I) {
+  const double nrm = std::sqrt(pt.kdir[0] * pt.kdir[0] + pt.kdir[1] * pt.kdir[1] + pt.kdir[2] * pt.kdir[2]);
+  if (!(nrm > 0) || !(pt.k0 > 0) || !std::isfinite(pt.kappa)) return fail(p, GSM_ERR_ARG, "bad point (k0, kdir, kappa)");
+  for (int a = 0; a < 3; ++a) I.kinc[a] = pt.kappa * pt.kdir[a] / nrm;
+  I.kb2 = pt.k0 * pt.k0 * p->d.eps_b[0];
+  for (int i = 0; i < 6; ++i) I.a[i] = pt.pol[i];
+  I.pc_c = 0.0;     // preconditioner off (identity) unless the solve sets it
+  I.pc_beta = 1.0;
+  // Eq. 4 needs k_m^2 != k_b^2 for every harmonic (text after Eq. 4)
+  const double tol = 1e-9 * I.kb2;
+  if (min_gap(I, g, I.kb2, 2.0 * tol) <= tol)
+    return fail(p, GSM_ERR_SINGULAR, "harmonic on the basis light cone (k_m^2 = k_b^2); shift kappa or eps_b");
+  return GSM_OK;
 }
 
 // Right preconditioner of the refined and FP64 GMRES solves (not in the
@@ -612,7 +603,8 @@ static void set_precond(Inst &I, const Geo &g, double d0) {
   for (double s = 1.0; s >= 0.125; s *= 0.5) {
     const double sd = s * d0;
     if (1.0 + sd < 0.1) continue;
-    if (min_gap(I, g, I.kb2 * (1.0 + sd)) < 0.1 * std::fabs(sd) * I.kb2) continue;
+    const double cut = 0.1 * std::fabs(sd) * I.kb2;
+    if (min_gap(I, g, I.kb2 * (1.0 + sd), cut) < cut) continue;
     I.pc_c = sd * I.kb2;
     I.pc_beta = 1.0 / (1.0 + sd);
     return;
