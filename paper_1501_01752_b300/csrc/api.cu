@@ -583,8 +583,9 @@ static gsm_status make_inst(gsm_plan_t *p, const gsm_point &pt, const Geo &g, In
   return GSM_OK;
 }
 
-// Right preconditioner of the refined and FP64 GMRES solves (not in the
-// paper, which iterates on Eq. 4 as it stands): M = I - s Delta_0 G(m), the
+// Right preconditioner of the Eq. 4 Krylov solves, GMRES and BiCGSTAB,
+// refined and FP64 (not in the paper, which iterates on Eq. 4 as it
+// stands): M = I - s Delta_0 G(m), the
 // block diagonal of Eq. 4 (the m - m' = 0 term of the Toeplitz product, i.e.
 // the Green tensor of the cell-averaged medium).  With G = g k_b^2 P_T - P_L
 // (g = 1/(k_m^2 - k_b^2), P_L = k k^T / k^2, P_T = I - P_L) its inverse is
