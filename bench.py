@@ -134,6 +134,14 @@ def cpu_baseline(points, budget_s=20.0):
                       % (done, len(points), cores)}
 
 
+def workload_config(args, ws):
+    """The config object of the JSON line, the same for both arms."""
+    return {"workload": "woodpile eps 11.9 in eps_b 1, Lambda 0.35, 31^3 harmonics, 64^3 FFT grid",
+            "global_batch": args.batch * ws, "tol": TOL, "krylov": args.krylov, "form": args.form.upper(),
+            "precond": args.precond, "l2": "flushed between steps (inputs+basis > L2)",
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -160,8 +168,7 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)",
-            "data": "synthetic", "config": {"workload": "woodpile eps 11.9, 31^3 harmonics, 64^3 grid",
-                                            "global_batch": args.batch, "tol": TOL},
+            "data": "synthetic", "config": workload_config(args, ws),
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -346,11 +353,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec + c128 refinement", "data": "synthetic",
-        "config": {"workload": "woodpile eps 11.9 in eps_b 1, Lambda 0.35, 31^3 harmonics, 64^3 FFT grid",
-                   "global_batch": B * ws, "tol": TOL, "krylov": args.krylov, "form": args.form.upper(),
-                   "precond": args.precond,
-                   "l2": "flushed between steps (inputs+basis > L2)",
-                   "parallelism": "replicas" if ws > 1 else "single"},
+        "config": workload_config(args, ws),
         "fp64_plain": None if fp64_value is None else
         {"value": fp64_value, "unit": "solves/s", "iters_mean": float(np.mean([i["iters"] for i in infos64]))},
         "speedup_vs_fp64": None if fp64_value is None else value / ws / fp64_value,
