@@ -47,6 +47,15 @@ def test_plan_query_fft_sizes_and_validation(gsm):
     assert small < big
 
 
+def test_plan_query_validates_preconditioner_choice(gsm):
+    L = (ctypes.c_int * 3)()
+    nb = ctypes.c_size_t()
+    for pc, want in ((gsm.PRECOND_AUTO, gsm.GSM_OK), (gsm.PRECOND_NONE, gsm.GSM_OK), (7, gsm.GSM_ERR_ARG)):
+        d = gsm._desc((0.3,) * 3, (5, 5, 5), 1.0, gsm.FP32_REFINE, 0, 0, 0.0, 0.0, 0, 0, 0, None, (0, 0, 0),
+                      precond=pc)
+        assert gsm.lib.gsm_plan_query(ctypes.byref(d), L, ctypes.byref(nb)) == want, pc
+
+
 def _physics_like_response():
     kap = np.linspace(9.0, 11.0, 16)
     xi = 0.7 / (kap - 10.13) + 0.3 - 0.05 * kap
