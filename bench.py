@@ -195,6 +195,8 @@ def main():
                     help="outer-residual arithmetic of the refined solve (double-float where available, or FP64)")
     ap.add_argument("--precond", default="auto", choices=["auto", "none"],
                     help="averaged-medium right preconditioner of the Krylov solves (auto) or none")
+    ap.add_argument("--sweep-batch", type=int, default=128,
+                    help="instances per launch of the sweep workload (points are grouped by truncation)")
     ap.add_argument("--workload", default="woodpile",
                     choices=["woodpile", "matvec", "sweep", "gyroid", "adjoint", "optimise"])
     args = ap.parse_args()

@@ -105,7 +105,8 @@ def sweep(args):
     st = wl.ellipsoid_lattice(period=1.0)
     f = 4 * math.pi / 3 * 0.4 * 0.3 * 0.2
     n_mg = math.sqrt(_mg(6.0, 1.0, f))
-    plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=64, precond=_pc(args))
+    mb = getattr(args, "sweep_batch", 128)
+    plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=mb, precond=_pc(args))
     pts, groups = [], []
     for gi in range(16):
         ratio = 0.10 + 0.02 * gi
@@ -138,7 +139,7 @@ def sweep(args):
     iters = [i["iters"] for i in infos]
     print(json.dumps({
         "workload": "sweep: ellipsoid lattice eps 6, 16 omega x 16 kappa x 2 pol, N = 15/21/31",
-        "precond": getattr(args, "precond", "auto"), "solves": len(pts), "seconds": t_sweep, "solves_per_s": len(pts) / t_sweep,
+        "precond": getattr(args, "precond", "auto"), "max_batch": mb, "solves": len(pts), "seconds": t_sweep, "solves_per_s": len(pts) / t_sweep,
         "retrieval_host_ms": 1000 * t_fit, "iters_mean": float(np.mean(iters)),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "eps_xx_by_ratio": out[0::2], "eps_yy_by_ratio": out[1::2], "n_MG": n_mg}), flush=True)
