@@ -47,11 +47,11 @@ _U = 3 * N_HARM[0] ** 3
 _TSZ = 3 * L_FFT * N_HARM[1] * N_HARM[2]
 OWN_MV = 8 * (_U + _TSZ) + 16 * _TSZ + 8 * (_TSZ + 2 * _U) + 4 * N_HARM[0] ** 3
 # dram__bytes_read.sum + dram__bytes_write.sum of the three product kernels
-# for one product launch at the bench batch (128 instances), from the ncu
-# capture summarised in profiles/traffic_c64_product_woodpile31_batch128.md
-# (mean of two products: 915.0 and 913.0 MB); None once a product kernel
+# for one product launch at the bench batch (512 instances), from the ncu
+# capture summarised in profiles/traffic_c64_product_woodpile31_batch512.md
+# (mean of two products: 4087.9 and 4082.6 MB); None once a product kernel
 # changes after that capture
-NCU_TRAFFIC = 0.914e9
+NCU_TRAFFIC = 4.0853e9
 
 
 def peaks():
@@ -179,7 +179,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=512,
+                    help="points per batched solve (measured on one B300: 32: 2834, 64: 3186, 128: 3457, "
+                         "256: 3596, 512: 3853, 1024: 3547 solves/s)")
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--alt-steps", type=int, default=5,
@@ -344,9 +346,7 @@ def main():
     achieved = B * B_MV / t_mv / 1e9 if t_mv > 0 else 0.0
     own = (B * OWN_MV + 4 * L_FFT ** 3) / t_mv / 1e9 if t_mv > 0 else 0.0
     # Gram-Schmidt passes (dots + update) inside the profiled solve, at the
-    # algorithmic bytes of all B instances per launch: an upper bound, since
-    # instances that converged earlier are masked (the smallest active share
-    # of the batch is about mean / max iterations)
+    # algorithmic bytes of the instances still iterating at each step
     kr_ms = kinds["krylov_dots"][1] + kinds["krylov_update"][1]
     kr_by = kinds["krylov_dots"][2] + kinds["krylov_update"][2]
     iters = [i["iters"] for i in infos]
@@ -372,8 +372,8 @@ def main():
                             "achieved": kr_by / (kr_ms / 1000.0) / 1e9 if kr_ms > 0 else None,
                             "peak": peak, "unit": "GB/s",
                             "frac": (kr_by / (kr_ms / 1000.0) / 1e9) / peak if kr_ms > 0 else None,
-                            "bound_kind": "upper (masked instances counted)",
-                            "active_share_min": float(np.mean(iters) / max(iters))},
+                            "bytes": "active instances per step",
+                            },
         "kernel_shares": {k: {"launches": v[0], "ms": v[1], "share": v[1] / tot_ms if tot_ms else None}
                           for k, v in kinds.items()},
         "profiled_ms_per_step": 1000 * t_prof / args.steps,

@@ -1070,6 +1070,16 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       // flags every CHECK steps (converged instances are masked meanwhile)
       constexpr int CHECK = 4;
       for (int j = 0; j < m; ++j) {
+        if (prof) {
+          // profiling: the bytes of this step's Gram-Schmidt passes count the
+          // instances still iterating (read before every step, outside the
+          // per-kernel events)
+          CK(cudaMemcpyAsync(h_act, k.act, B * 4, cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          k.nact = 0;
+          for (int b = 0; b < B; ++b) k.nact += h_act[b] != 0;
+          if (!k.nact) break;
+        }
         mv.X = V + (long long)j * Us;
         mv.Y = V + (long long)(j + 1) * Us;
         CK(matvec<R>(p, lv, mv, prof));

@@ -145,6 +145,8 @@ struct KrylovPtrs {
   double *scale64;          // [B]
   double *resid;            // [B]
   int force_reorth;         // 0: DGKS test, 1: always reorthogonalise, 2: never
+  int nact;                 // profiling only: instances active in the step launched (0 = all B);
+                            // the recorded bytes of the Gram-Schmidt passes count these
   int *jdev;                // graph mode: Arnoldi step counter on the device (nullptr: host j)
 };
 

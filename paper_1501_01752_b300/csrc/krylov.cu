@@ -496,7 +496,8 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
   // current step only take part in the completion count
   const int ngroups = k.jdev ? (k.m + GV - 1) / GV : (nv + GV - 1) / GV;
   dim3 gdots(k.nblk * ngroups, k.B);
-  const double vb = (double)sizeof(typename Cx<R>::T) * k.U * k.B;  // logical bytes per vector batch
+  // logical bytes per vector over the instances still iterating
+  const double vb = (double)sizeof(typename Cx<R>::T) * k.U * (k.nact > 0 ? k.nact : k.B);
   if (prof) prof->begin(KIND_DOTS, st);
   k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs, k.nblk, k.jdev);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
