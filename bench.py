@@ -297,6 +297,13 @@ def main():
     e2e = B * ws * ee_steps / (time.perf_counter() - t0)
     h2d = B * 96  # per-point parameter block copied to the device: k_inc, k_b^2, polarisation, preconditioner (12 doubles)
     d2h = B * U * 16
+    # the retrieval workflow's call: gsm_sweep returns only the 0th-order
+    # amplitudes E_0 (3 complex128 per point) to the host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ee_steps):
+        plan.sweep(pts)
+    e2e_sweep = B * ws * ee_steps / (time.perf_counter() - t0)
 
     # the other Krylov method on the same batch (few steps; not the headline)
     alt = "bicgstab" if args.krylov == "gmres" else "gmres"
@@ -378,6 +385,8 @@ def main():
                           for k, v in kinds.items()},
         "profiled_ms_per_step": 1000 * t_prof / args.steps,
         "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e_sweep": {"value": e2e_sweep, "unit": "solves/s", "call": "gsm_sweep (E_0 only)",
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": B * 48},
         "gpu_launches": int(launches),
         "autotuned_blocks": list(plan.tuned_blocks(gsm.FP32_REFINE)),
         "clocks": clk,
