@@ -49,9 +49,9 @@ OWN_MV = 8 * (_U + _TSZ) + 16 * _TSZ + 8 * (_TSZ + 2 * _U) + 4 * N_HARM[0] ** 3
 # dram__bytes_read.sum + dram__bytes_write.sum of the three product kernels
 # for one product launch at the bench batch (512 instances), from the ncu
 # capture summarised in profiles/traffic_c64_product_woodpile31_batch512.md
-# (mean of two products: 4087.9 and 4082.6 MB); None once a product kernel
+# (mean of two products: 4086.2 and 4088.5 MB); None once a product kernel
 # changes after that capture
-NCU_TRAFFIC = 4.0853e9
+NCU_TRAFFIC = 4.0874e9
 
 
 def peaks():

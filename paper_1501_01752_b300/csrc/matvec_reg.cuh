@@ -341,10 +341,15 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
 // 32 banks evenly.
 __host__ __device__ __forceinline__ int p3_pitch(int N0) { return (N0 + 15) / 16 * 16 + 8; }
 
-// (component, row) items per lane team in pass 3: two for 32/64-point teams
-// (twice the loads in flight per thread), one for the 128-point teams, whose
-// registers are already taken by the longer transforms
-template <int L0> __host__ __device__ constexpr int p3_items() { return L0 <= 64 ? 2 : 1; }
+// (component, row) items per lane team in pass 3, all loads issued before the
+// first transform: for 32/64-point teams three with 8-byte values (complex64:
+// a team then holds the three components of one row; 330 against 367 us per
+// launch with two at batch 512) and two with 16-byte values (complex128 and
+// double-float, whose registers would grow past 170 with three); one for the
+// 128-point teams, whose registers are already taken by the longer transforms
+template <int L0, typename R> __host__ __device__ constexpr int p3_items() {
+  return L0 <= 64 ? (sizeof(typename Cx<R>::T) == 8 ? 3 : 2) : 1;
+}
 
 // Pass 2 for complex64 with 64-point y and z transforms, two x frequencies
 // (r_x, r_x + 1) per block: every lane runs the transforms of both planes at
@@ -472,7 +477,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     X += (long long)(*jdev) * jstride;
     Y += (long long)(*jdev) * jstride;
   }
-  constexpr int TS = F::TS, NTM = TT / TS, IPT = p3_items<L0>();
+  constexpr int TS = F::TS, NTM = TT / TS, IPT = p3_items<L0, R>();
   __shared__ C bufs[NTM * F::BUF];
   __shared__ double red[32];
   extern __shared__ __align__(16) unsigned char sm_dyn[];
@@ -620,8 +625,9 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
 }
 
 
+template <typename R>
 static int p3_rows(const Geo &g, int tb) {
-  const int items = (tb / (g.L[0] / 8)) * (g.L[0] <= 64 ? p3_items<64>() : p3_items<128>());
+  const int items = (tb / (g.L[0] / 8)) * (g.L[0] <= 64 ? p3_items<64, R>() : p3_items<128, R>());
   return items / 3;
 }
 
@@ -710,7 +716,7 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   const Geo &g = a.g;
   if (g.L[0] == 128) {
     constexpr int TX = tt128<R, TT>();
-    const int rows = p3_rows(g, TX);
+    const int rows = p3_rows<R>(g, TX);
     const size_t smem = sizeof(C) * 3 * (size_t)rows * p3_pitch(g.N[0]) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
     dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);
 #define GSM_P3X(M, HF)                                                                                           \
@@ -723,7 +729,7 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
 #undef GSM_P3X
     return;
   }
-  const int rows = p3_rows(g, TT);
+  const int rows = p3_rows<R>(g, TT);
   const size_t smem = sizeof(C) * 3 * (size_t)rows * p3_pitch(g.N[0]) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
   dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);
 #define GSM_P3(L0, M, HF)                                                                                         \

@@ -31,7 +31,9 @@ bool reg_path_ok(const Geo &g) {
 
 int matvec_reg_blocks_pass3(const Geo &g) {
   if (!reg_path_ok(g)) return 1;
-  const int rows = p3_rows(g, 128);   // the smallest block the autotuner may pick
+  // the smallest block the autotuner may pick, with the fewest items per team
+  // (16-byte values): the most blocks any precision launches
+  const int rows = p3_rows<double>(g, 128);
   return (int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows);
 }
 
