@@ -344,7 +344,7 @@ __host__ __device__ __forceinline__ int p3_pitch(int N0) { return (N0 + 15) / 16
 // (component, row) items per lane team in pass 3, all loads issued before the
 // first transform: for 32/64-point teams three with 8-byte values (complex64:
 // a team then holds the three components of one row; 330 against 367 us per
-// launch with two at batch 512) and two with 16-byte values (complex128 and
+// launch with two and 390 with four, at batch 512) and two with 16-byte values (complex128 and
 // double-float, whose registers would grow past 170 with three); one for the
 // 128-point teams, whose registers are already taken by the longer transforms
 template <int L0, typename R> __host__ __device__ constexpr int p3_items() {
