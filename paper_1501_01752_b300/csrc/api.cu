@@ -214,9 +214,16 @@ static int capped_restart(const gsm_plan_desc &d, const Geo &g, int B, int prec)
 
 static long long padded(long long U) { return ((U + 63) / 64) * 64; }
 
+// Blocks per instance of the vector kernels (Gram-Schmidt passes, solution
+// update, residual update): about KRYLOV_GRID blocks across the batch (one
+// wave of 4 blocks of 256 threads per SM), each block at least 2048
+// elements.  B' * krylov_blocks(g, B') <= KRYLOV_GRID + B' for every batch
+// B', which sizes the partial-sum buffer.  Four waves (16 per SM) measured
+// +0.8% at batch 512 but -8% at batch 64 and -1.7% on the ellipsoid sweep:
+// each block then spreads its fixed reduction work over fewer tiles.
+constexpr long long KRYLOV_GRID = 4LL * 148;
 static int krylov_blocks(const Geo &g, int B) {
-  // enough blocks for ~4 waves of 148 SMs across the batch, each >= 2048 elements
-  long long per = std::max(1LL, (4LL * 148 + B - 1) / B);
+  long long per = std::max(1LL, (KRYLOV_GRID + B - 1) / B);
   long long cap = std::max(1LL, (padded(g.U) + 2047) / 2048);
   return (int)std::min(per, cap);
 }
@@ -253,8 +260,8 @@ static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nbl
   k.U = g.U;
   k.Us = padded(g.U);
   k.nblk = nblk;
-  // partials for any batch <= B: B' * krylov_blocks(g, B') <= 4 * 148 + B'
-  k.partial = (double *)take((size_t)(4 * 148 + B) * hs * 8);
+  // partials for any batch <= B: B' * krylov_blocks(g, B') <= KRYLOV_GRID + B'
+  k.partial = (double *)take((size_t)(KRYLOV_GRID + B) * hs * 8);
   k.counter = (unsigned *)take((size_t)B * 4);
   k.hdot0 = (double *)take((size_t)B * hs * 8);
   k.hdot1 = (double *)take((size_t)B * hs * 8);
