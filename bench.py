@@ -112,9 +112,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(points, budget_s=20.0):
+def cpu_baseline(points, budget_s=20.0, fields=None):
     """The oracle (FP64 GMRES, scipy FFT on all host cores) on a bounded sample
-    of the batch: as many points as fit in about budget_s seconds."""
+    of the batch: as many points as fit in about budget_s seconds.  The
+    oracle's fields are appended to `fields` when a list is given."""
     from oracle import operator as oop
     from oracle import retrieval as ort
     cores = os.cpu_count() or 1
@@ -124,7 +125,9 @@ def cpu_baseline(points, budget_s=20.0):
     Delta = ost.delta(N_HARM, 1.0)
     done, t0 = 0, time.perf_counter()
     for p in points:
-        ort.solve_point(ost, N_HARM, 1.0, p["k0"], p["kdir"], p["kappa"], p["pol"], tol=TOL, Delta=Delta)
+        Eo, _ = ort.solve_point(ost, N_HARM, 1.0, p["k0"], p["kdir"], p["kappa"], p["pol"], tol=TOL, Delta=Delta)
+        if fields is not None:
+            fields.append(np.asarray(Eo).ravel())
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -392,7 +395,14 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(pts)
+        oracle_fields = []
+        line["cpu_baseline"] = cpu_baseline(pts, fields=oracle_fields)
+        # the refined complex64 fields of the e2e solves against the oracle's
+        # FP64 fields of the same points (both to relative residual 1e-8)
+        Eg = Eh.numpy()
+        errs = [float(np.linalg.norm(Eg[i * U:(i + 1) * U] - f) / np.linalg.norm(f)) for i, f in enumerate(oracle_fields)]
+        line["oracle_parity"] = {"points": len(errs), "field_rel_err_max": max(errs) if errs else None,
+                                 "note": "GPU FP32+refine vs oracle FP64 GMRES, both to residual 1e-8"}
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
