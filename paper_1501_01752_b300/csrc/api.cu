@@ -631,7 +631,9 @@ static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a
     // the double-float product exists only on the lane-team path (callers check)
     return launch_matvec_reg<dfl>(a, st, prof, nullptr);
   } else {
-    if (!p->team_only && a.mode < 2 && reg_path_ok(a.g))
+    // the lane-team kernels take the forward and residual forms of both
+    // equations and the adjoint forms of Eq. 4
+    if (!p->team_only && (a.mode < 2 || a.form == 0) && reg_path_ok(a.g))
       return launch_matvec_reg<R>(a, st, prof, lv.tb[sizeof(R) == 4 ? 1 : 0]);
     if (a.pc) return cudaErrorInvalidValue;   // the preconditioned product exists only on the lane-team path
     return launch_matvec<R>(a, st, prof);

@@ -98,7 +98,8 @@ template <typename R> struct MatvecArgs {
 };
 
 template <typename R> cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof);
-// team-of-lanes FFT path for FFT sizes 32/64 on every axis (modes 0, 1)
+// team-of-lanes FFT path for FFT sizes 32/64 on every axis, cubic 128 (modes
+// 0, 1; modes 2, 3 for Eq. 4)
 bool reg_path_ok(const Geo &g);
 template <typename R>
 cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof, const int *tb);

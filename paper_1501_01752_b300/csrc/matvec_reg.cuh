@@ -151,7 +151,9 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
 // team per (m_z, m_y) row holding all three components of the row, so that
 // the scaled write-back of a Krylov vector and the map read and write only
 // the team's own values.  op 0: k_m x x (H-field form, Eq. 5); op 1: M^{-1} x
-// (right preconditioner of Inst, Eq. 4; iden = 1/(k_m^2 - k_b^2)).
+// (right preconditioner of Inst, Eq. 4; iden = 1/(k_m^2 - k_b^2)); op 2:
+// G(m) x (the adjoint of Eq. 4, A^H v = v - T (G v): G is real and symmetric
+// for real k and k_b, and T Hermitian for real eps).
 template <typename R, int L0, int TT>
 __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__restrict__ X, long long xstride,
                                                   typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
@@ -217,6 +219,16 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
         v[0][a] = mk(al * u[0].x + f * kx * ku.x, al * u[0].y + f * kx * ku.y);
         v[1][a] = mk(al * u[1].x + f * ky * ku.x, al * u[1].y + f * ky * ku.y);
         v[2][a] = mk(al * u[2].x + f * kz * ku.x, al * u[2].y + f * kz * ku.y);
+        continue;
+      }
+      if (op == 2) {
+        // G u = (k_b^2 u - k (k . u)) / (k_m^2 - k_b^2) (zero where no harmonic sits)
+        if (!valid || h < 0) continue;
+        const R id = idr[h], kb2 = (R)inst[b].kb2;
+        const C ku = mk(kx * u[0].x + ky * u[1].x + kz * u[2].x, kx * u[0].y + ky * u[1].y + kz * u[2].y);
+        v[0][a] = mk(id * (kb2 * u[0].x - kx * ku.x), id * (kb2 * u[0].y - kx * ku.y));
+        v[1][a] = mk(id * (kb2 * u[1].x - ky * ku.x), id * (kb2 * u[1].y - ky * ku.y));
+        v[2][a] = mk(id * (kb2 * u[2].x - kz * ku.x), id * (kb2 * u[2].y - kz * ku.y));
         continue;
       }
     }
@@ -461,7 +473,8 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, c
 
 
 // MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u); HF = 1 (Eq. 5): G u is
-// replaced by k_m x u / (k_m^2 - k_b^2)
+// replaced by k_m x u / (k_m^2 - k_b^2).  nog = 1 (adjoint of Eq. 4, G
+// already applied in pass 1): G u is replaced by u.
 template <typename R, int L0, int MODE, int TT, int HF>
 __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T *__restrict__ T,
                                                  const typename Io<R>::T *__restrict__ X, long long xstride,
@@ -469,7 +482,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
                                                  const int *__restrict__ act, const Inst *__restrict__ inst,
                                                  const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,
                                                  int rows, double *partial, unsigned *counter, double *norm_out,
-                                                 const int *__restrict__ jdev, long long jstride, int pc) {
+                                                 const int *__restrict__ jdev, long long jstride, int pc, int nog) {
   using C = typename Cx<R>::T;
   using IO = typename Io<R>::T;
   using F = Team8<L0>;
@@ -568,6 +581,10 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       y0 = csub(y0, cscale(csub(cscale(u2, ky), cscale(u1, kz)), id));
       y1 = csub(y1, cscale(csub(cscale(u0, kz), cscale(u2, kx)), id));
       y2 = csub(y2, cscale(csub(cscale(u1, kx), cscale(u0, ky)), id));
+    } else if (nog) {
+      y0 = csub(y0, u0);
+      y1 = csub(y1, u1);
+      y2 = csub(y2, u2);
     } else {
       if constexpr (!std::is_same<R, dfl>::value) {
         if (pc) {
@@ -645,10 +662,11 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
   const Geo &g = a.g;
   if (g.L[0] == 128) {
     constexpr int TX = tt128<R, TT>();
-    if (a.form || a.pc) {
+    if (a.form || a.pc || a.mode >= 2) {
       dim3 gridh((int)(((long long)g.N[2] * g.N[1] + TX / 16 - 1) / (TX / 16)), a.B);
       k_fwd_x_t8h<R, 128, TX><<<gridh, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
-                                                    a.tw, a.jdev, a.jstride, a.form ? 0 : 1, a.iden);
+                                                    a.tw, a.jdev, a.jstride, a.form ? 0 : (a.mode >= 2 ? 2 : 1),
+                                                    a.iden);
     } else {
       const int RB = TX / 16 * P1_RPT;
       dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
@@ -659,9 +677,9 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
   }
   const int RB = TT / (g.L[0] / 8) * P1_RPT;
   dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
-  if (a.form || a.pc) {
+  if (a.form || a.pc || a.mode >= 2) {
     const int RBH = TT / (g.L[0] / 8);
-    const int op = a.form ? 0 : 1;
+    const int op = a.form ? 0 : (a.mode >= 2 ? 2 : 1);
     dim3 gridh((int)(((long long)g.N[2] * g.N[1] + RBH - 1) / RBH), a.B);
     if (g.L[0] == 64)
       k_fwd_x_t8h<R, 64, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
@@ -723,9 +741,9 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   cudaFuncSetAttribute(k_inv_x_t8<R, 128, M, TX, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
   k_inv_x_t8<R, 128, M, TX, HF><<<grid, TX, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,   \
                                                         a.iden, a.tw, rows, a.partial, a.counter, a.norm_out,     \
-                                                        a.jdev, a.jstride, a.pc)
-    if (a.form) { if (a.mode == 1) { GSM_P3X(1, 1); } else { GSM_P3X(0, 1); } }
-    else { if (a.mode == 1) { GSM_P3X(1, 0); } else { GSM_P3X(0, 0); } }
+                                                        a.jdev, a.jstride, a.pc, a.mode >= 2)
+    if (a.form) { if (a.mode & 1) { GSM_P3X(1, 1); } else { GSM_P3X(0, 1); } }
+    else { if (a.mode & 1) { GSM_P3X(1, 0); } else { GSM_P3X(0, 0); } }
 #undef GSM_P3X
     return;
   }
@@ -736,13 +754,13 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   cudaFuncSetAttribute(k_inv_x_t8<R, L0, M, TT, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
   k_inv_x_t8<R, L0, M, TT, HF><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,     \
                                                        a.iden, a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, \
-                                                       a.jstride, a.pc)
+                                                       a.jstride, a.pc, a.mode >= 2)
   if (g.L[0] == 64) {
-    if (a.form) { if (a.mode == 1) { GSM_P3(64, 1, 1); } else { GSM_P3(64, 0, 1); } }
-    else { if (a.mode == 1) { GSM_P3(64, 1, 0); } else { GSM_P3(64, 0, 0); } }
+    if (a.form) { if (a.mode & 1) { GSM_P3(64, 1, 1); } else { GSM_P3(64, 0, 1); } }
+    else { if (a.mode & 1) { GSM_P3(64, 1, 0); } else { GSM_P3(64, 0, 0); } }
   } else {
-    if (a.form) { if (a.mode == 1) { GSM_P3(32, 1, 1); } else { GSM_P3(32, 0, 1); } }
-    else { if (a.mode == 1) { GSM_P3(32, 1, 0); } else { GSM_P3(32, 0, 0); } }
+    if (a.form) { if (a.mode & 1) { GSM_P3(32, 1, 1); } else { GSM_P3(32, 0, 1); } }
+    else { if (a.mode & 1) { GSM_P3(32, 1, 0); } else { GSM_P3(32, 0, 0); } }
   }
 #undef GSM_P3
 }
