@@ -98,14 +98,16 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
     if (lane == 0) wsum[k][warp] = (double)sk;
   }
   __syncthreads();
-  // this block's share: dots i0..i1-1 (and ||w||^2 from group 0)
-  double *pb = partial + ((long long)b * nblk + blk) * K;
+  // this block's share: dots i0..i1-1 (and ||w||^2 from group 0).  The
+  // partials of one value lie together ([instance][value][block]), so that
+  // the last block reads each value's partials with coalesced loads.
+  double *pb = partial + (long long)b * nblk * ostride + blk;
   for (int k = threadIdx.x; k < 2 * ng + (grp == 0); k += blockDim.x) {
     const int src = k < 2 * ng ? k : 2 * GV;
     double s = 0;
 #pragma unroll
     for (int q = 0; q < NW; ++q) s += wsum[src][q];
-    pb[k < 2 * ng ? 2 * i0 + k : 2 * nv] = s;
+    pb[(long long)(k < 2 * ng ? 2 * i0 + k : 2 * nv) * nblk] = s;
     __threadfence();
   }
   __syncthreads();
@@ -115,10 +117,26 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
   }
   __syncthreads();
   if (!am_last) return;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double s = 0;
-    for (int q = 0; q < nblk; ++q) s += __ldcg(&partial[((long long)b * nblk + q) * K + k]);
-    out[(long long)b * ostride + k] = s;
+  const double *pin = partial + (long long)b * nblk * ostride;
+  if (nblk <= 16) {
+    // few blocks per instance (large batches): one thread per value
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const double *pk = pin + (long long)k * nblk;
+      double s = 0;
+      for (int q = 0; q < nblk; ++q) s += __ldcg(pk + q);
+      out[(long long)b * ostride + k] = s;
+    }
+  } else {
+    // hundreds of blocks per instance (small batches): one warp per value,
+    // the lanes across the partials (lane-strided sums, then the shuffle
+    // tree; a fixed order either way)
+    for (int k = warp; k < K; k += NW) {
+      const double *pk = pin + (long long)k * nblk;
+      double s = 0;
+      for (int q = lane; q < nblk; q += 32) s += __ldcg(pk + q);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) out[(long long)b * ostride + k] = s;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) counter[b] = 0;
