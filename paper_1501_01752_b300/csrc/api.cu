@@ -262,6 +262,7 @@ static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nbl
   k.nblk = nblk;
   // partials for any batch <= B: B' * krylov_blocks(g, B') <= KRYLOV_GRID + B'
   k.partial = (double *)take((size_t)(KRYLOV_GRID + B) * hs * 8);
+  k.alist = (int *)take((size_t)(B + 1) * 4);
   k.counter = (unsigned *)take((size_t)B * 4);
   k.hdot0 = (double *)take((size_t)B * hs * 8);
   k.hdot1 = (double *)take((size_t)B * hs * 8);
@@ -895,6 +896,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   k.B = B;
   k.m = m;
   k.nblk = krylov_blocks(g, B);
+  k.bcap = krylov_blocks(g, 1);
   // complex64 inner solves stop at inner_tol >= 1e-6, far above the level
   // (~1e-7 relative) where classical Gram-Schmidt without reorthogonalisation
   // loses orthogonality, so they skip the second pass; FP64 solves keep the
@@ -1094,7 +1096,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
         CK(matvec<R>(p, lv, mv, prof));
         CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
         CK(launch_finish(k, j, st));
-        p->launches += 3 + (k.force_reorth == 2 ? 2 : 4) + 1;
+        p->launches += 3 + 1 + (k.force_reorth == 2 ? 2 : 4) + 1;   // product, active list, Gram-Schmidt, finish
         if ((j + 1) % CHECK == 0 && j + 1 < m) {
           CK(cudaMemcpyAsync(h_act, k.act, B * 4, cudaMemcpyDeviceToHost, st));
           CK(cudaStreamSynchronize(st));
@@ -1143,7 +1145,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     if (cyc) {
       int steps_run = 0;
       for (int b = 0; b < B; ++b) steps_run = std::max(steps_run, need[b] ? h_kc[b] : 0);
-      p->launches += (long long)steps_run * (bicg ? 2 * 3 + 5 + 1 : 3 + (k.force_reorth == 2 ? 2 : 4) + 2);
+      p->launches += (long long)steps_run * (bicg ? 2 * 3 + 5 + 1 : 3 + 1 + (k.force_reorth == 2 ? 2 : 4) + 2);
     }
     for (int b = 0; b < B; ++b) {
       if (!need[b]) continue;

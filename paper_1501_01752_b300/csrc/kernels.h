@@ -129,6 +129,9 @@ struct KrylovPtrs {
   long long U;              // logical vector length (3 N^3)
   long long Us;             // stored stride: U rounded up to 64 (pads stay zero)
   int nblk;                 // blocks per instance for vector kernels
+  int bcap;                 // most blocks per instance (one 2048-element tile each): the
+                            // Gram-Schmidt passes spread nblk * B blocks over the active instances
+  int *alist;               // [B + 1]: number of active instances, then their indices
   double *partial;          // [B][nblk][2(m+1)+1]
   unsigned *counter;        // [B]
   double *hdot0, *hdot1;    // [B][2(m+1)+1] dots (+ ||w||^2 last)

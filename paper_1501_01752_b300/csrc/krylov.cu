@@ -42,13 +42,20 @@ template <typename R>
 __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict__ V, long long vinst, long long Us,
                                              int nv, int wi, const int *__restrict__ act,
                                              const int *__restrict__ gate, double *partial, unsigned *counter,
-                                             double *out, int ostride, int nblk, const int *__restrict__ jdev) {
+                                             double *out, int ostride, int nblk, const int *__restrict__ jdev,
+                                             const int *__restrict__ alist, int bcap) {
   using C = typename Cx<R>::T;
   constexpr int EPT = EptDots<R>::v, NW = KT / 32, CH = 4, NA = 2 * GV + 1;
   __shared__ double wsum[NA][NW];
   __shared__ int am_last;
-  const int b = blockIdx.y, blk = blockIdx.x % nblk, grp = blockIdx.x / nblk;
-  if (!act[b]) return;
+  // the active instances share the grid's blocks: slot a = blockIdx.x / nblk
+  const int nact = alist[0];
+  if (nact == 0) return;
+  nblk = min(bcap, max(nblk, (int)(gridDim.x / nact)));
+  const int a = blockIdx.x / nblk, blk = blockIdx.x % nblk, grp = blockIdx.y;
+  if (a >= nact) return;
+  const int b = alist[1 + a];
+  (void)act;
   if (gate && !gate[b]) return;
   if (jdev) {                        // graph mode: the step comes from the device counter
     nv = *jdev + 1;
@@ -101,7 +108,7 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
   // this block's share: dots i0..i1-1 (and ||w||^2 from group 0).  The
   // partials of one value lie together ([instance][value][block]), so that
   // the last block reads each value's partials with coalesced loads.
-  double *pb = partial + (long long)b * nblk * ostride + blk;
+  double *pb = partial + (long long)a * nblk * ostride + blk;
   for (int k = threadIdx.x; k < 2 * ng + (grp == 0); k += blockDim.x) {
     const int src = k < 2 * ng ? k : 2 * GV;
     double s = 0;
@@ -113,11 +120,11 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned t = atomicAdd(&counter[b], 1u);
-    am_last = (t == (unsigned)gridDim.x - 1);
+    am_last = (t == (unsigned)(nblk * gridDim.y) - 1);
   }
   __syncthreads();
   if (!am_last) return;
-  const double *pin = partial + (long long)b * nblk * ostride;
+  const double *pin = partial + (long long)a * nblk * ostride;
   if (nblk <= 16) {
     // few blocks per instance (large batches): one thread per value
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -148,7 +155,8 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
                                                int nv, int wi, const double *__restrict__ h, int hstride,
                                                const int *__restrict__ act, const int *__restrict__ gate,
                                                double *partial, unsigned *counter, double *wn_out,
-                                               int *gate_out, int force, const int *__restrict__ jdev) {
+                                               int *gate_out, int force, const int *__restrict__ jdev,
+                                               const int *__restrict__ alist, int nblk, int bcap) {
   using C = typename Cx<R>::T;
   constexpr int EPT = Ept<R>::v;
   if (jdev) {
@@ -157,8 +165,14 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
   }
   __shared__ C hs[MAXM + 1];
   __shared__ double red[32];
-  const int b = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
-  if (!act[b]) return;
+  // the active instances share the grid's blocks, as in k_dots
+  const int nact = alist[0];
+  if (nact == 0) return;
+  nblk = min(bcap, max(nblk, (int)(gridDim.x / nact)));
+  const int a = blockIdx.x / nblk, blk = blockIdx.x % nblk;
+  if (a >= nact) return;
+  const int b = alist[1 + a];
+  (void)act;
   if (gate && !gate[b]) return;
   for (int i = threadIdx.x; i < nv; i += blockDim.x)
     hs[i] = mk((R)h[(long long)b * hstride + 2 * i], (R)h[(long long)b * hstride + 2 * i + 1]);
@@ -197,7 +211,7 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
     for (int k = 0; k < EPT; ++k) n2 += w[k].x * w[k].x + w[k].y * w[k].y;
     acc += (double)n2;
   }
-  if (last_block_sum(acc, red, partial, counter, wn_out, b, nblk, blk)) {
+  if (last_block_sum(acc, red, partial + (long long)a * nblk, counter + b, wn_out + b, 0, nblk, blk)) {
     if (gate_out && threadIdx.x == 0) {
       const double before = h[(long long)b * hstride + 2 * nv];
       gate_out[b] = (force == 1 || (force == 0 && wn_out[b] < 0.5 * before)) ? 1 : 0;
@@ -504,32 +518,66 @@ __global__ void k_extract_e0(const double2 *x64, long long xinst, Geo g, int B, 
   out[t] = x64[b * xinst + c * g.Nh + h0];
 }
 
+// The active instances in increasing order: alist[0] = count, alist[1 + a]
+// = index of the a-th active instance.  One block, chunks of its width.
+__global__ void k_active_list(const int *__restrict__ act, int B, int *alist) {
+  __shared__ int wc[32];
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < B; c0 += blockDim.x) {
+    const int b = c0 + threadIdx.x;
+    const bool on = b < B && act[b] != 0;
+    const unsigned msk = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) wc[w] = __popc(msk);
+    __syncthreads();
+    int off = base;
+    for (int q = 0; q < w; ++q) off += wc[q];
+    if (on) alist[1 + off + __popc(msk & ((1u << lane) - 1u))] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int q = 0; q < nw; ++q) t += wc[q];
+      base += t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) alist[0] = base;
+}
+
 // ------------------------------------------------------------ launchers
 template <typename R>
 cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long long vinst, int j, cudaStream_t st,
                                  Profiler *prof) {
   const int nv = j + 1, wi = j + 1, hs = 2 * (k.m + 1) + 1;
-  dim3 grid(k.nblk, k.B);
+  // nblk * B blocks, spread over the instances still iterating (at least
+  // nblk each, at most bcap): a step where few instances remain streams
+  // their basis with as many blocks as a full batch
+  k_active_list<<<1, 1024, 0, st>>>(k.act, k.B, k.alist);
+  dim3 grid(k.nblk * k.B);
   // graph mode sizes the dots grid for the longest basis; blocks past the
   // current step only take part in the completion count
   const int ngroups = k.jdev ? (k.m + GV - 1) / GV : (nv + GV - 1) / GV;
-  dim3 gdots(k.nblk * ngroups, k.B);
+  dim3 gdots(k.nblk * k.B, ngroups);
   // logical bytes per vector over the instances still iterating
   const double vb = (double)sizeof(typename Cx<R>::T) * k.U * (k.nact > 0 ? k.nact : k.B);
   if (prof) prof->begin(KIND_DOTS, st);
-  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs, k.nblk, k.jdev);
+  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs, k.nblk, k.jdev,
+                                    k.alist, k.bcap);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot0, hs, k.act, nullptr, k.partial, k.counter, k.wn0,
-                                   k.gate, k.force_reorth, k.jdev);
+                                   k.gate, k.force_reorth, k.jdev, k.alist, k.nblk, k.bcap);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   if (k.force_reorth == 2) return cudaGetLastError();   // no second pass: gate was cleared
   if (prof) prof->begin(KIND_DOTS, st);
-  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs, k.nblk, k.jdev);
+  k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs, k.nblk, k.jdev,
+                                    k.alist, k.bcap);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot1, hs, k.act, k.gate, k.partial, k.counter, k.wn1,
-                                   nullptr, 0, k.jdev);
+                                   nullptr, 0, k.jdev, k.alist, k.nblk, k.bcap);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   return cudaGetLastError();
 }
