@@ -42,16 +42,24 @@ B_MV = 8 * 3 * (2 * N_HARM[0] ** 3 + 4 * L_FFT ** 2 * N_HARM[0]) + 4 * L_FFT ** 
 # Bytes this implementation's x-first layout actually moves per instance and
 # product (3 L N^2 intermediate): x-forward s_c (U + 3 L N^2), yz pass
 # 2 s_c 3 L N^2, x-inverse + Green s_c (3 L N^2 + 2 U) + 4 N^3, plus the
-# multiplier once per launch.
+# multiplier once per launch.  The preconditioned product of the solves adds
+# the scaled input written back by pass 1 (s_c U) and the per-harmonic
+# denominators read by its three-component pass 1 (4 N^3).
 _U = 3 * N_HARM[0] ** 3
 _TSZ = 3 * L_FFT * N_HARM[1] * N_HARM[2]
 OWN_MV = 8 * (_U + _TSZ) + 16 * _TSZ + 8 * (_TSZ + 2 * _U) + 4 * N_HARM[0] ** 3
-# dram__bytes_read.sum + dram__bytes_write.sum of the three product kernels
-# for one product launch at the bench batch (512 instances), from the ncu
-# capture summarised in profiles/traffic_c64_product_woodpile31_batch512.md
-# (mean of two products: 4086.2 and 4088.5 MB); None once a product kernel
-# changes after that capture
-NCU_TRAFFIC = 4.0874e9
+OWN_MV_PC = OWN_MV + 8 * _U + 4 * N_HARM[0] ** 3
+# dram__bytes_read.sum + dram__bytes_write.sum of the three kernels of one
+# product launch at the bench batch (512 instances), from one ncu capture of
+# the current kernels, per operator; None where no capture of the current
+# kernels exists.
+NCU_TRAFFIC = {"precond": 4.5105e9, "plain": 4.0812e9}
+# FP64 work of one FP64 product of one instance on this grid, from one ncu
+# count of the three FP64 product kernels at 32 instances: floating-point
+# operations (2 DFMA + DADD + DMUL) and FP64-pipe instructions (DFMA + DADD +
+# DMUL, each one issue of the pipe); None until counted for the current kernels.
+FP64_FLOP_PER_PRODUCT = 55.347e6
+FP64_INSTR_PER_PRODUCT = 44.70e6
 
 
 def peaks():
@@ -326,64 +334,107 @@ def main():
         palt.close()
 
     # plain FP64 GPU path on the same batch (--fp64-steps 0 skips it)
-    fp64_value, infos64 = None, None
+    fp64_value, infos64, fp64_roof = None, None, None
     if args.fp64_steps > 0:
         p64 = make_plan(gsm.FP64)
         p64.solve(pts, out=E)
         t64, infos64 = timed(p64, args.fp64_steps, E)
         fp64_value = B * args.fp64_steps / t64
         p64.close()
+        # the FP64 path against the measured FP64 FMA rate: every product of
+        # every instance (Krylov products + FP64 residuals) per second
+        fp64_peak = gsm.probe_fma(0, local, stream.cuda_stream)
+        prods = sum(i["iters"] + i["refine_steps"] for i in infos64) * args.fp64_steps / t64
+        fp64_roof = {"bound": "alu (FP64 pipe)", "peak": fp64_peak, "unit": "TFLOP/s",
+                     "peak_kind": "measured (gsm_probe_fma FP64)", "instance_products_per_s": prods,
+                     "achieved": None if FP64_FLOP_PER_PRODUCT is None else prods * FP64_FLOP_PER_PRODUCT / 1e12,
+                     "flop_per_product": FP64_FLOP_PER_PRODUCT,
+                     "scope": "product flops over the whole FP64 solve time (Gram-Schmidt not counted)"}
+        if FP64_FLOP_PER_PRODUCT is not None:
+            fp64_roof["frac"] = fp64_roof["achieved"] / fp64_peak
+            # issue share of the FP64 pipe (an FMA-only kernel at the probe's rate = 1)
+            fp64_roof["pipe_frac"] = prods * FP64_INSTR_PER_PRODUCT / (fp64_peak * 1e12 / 2)
 
     peak, peak_kind = peaks()
-    # The complex64 product (x-forward + yz convolution + x-inverse/Green) on
-    # the full batch with every instance active: R products through gsm_apply,
-    # each pass timed with CUDA events on the plan's stream.  (Inside a solve,
-    # instances that have converged are masked, so a launch there moves less
-    # than B instances' bytes.)
+    # The complex64 product on the full batch with every instance active,
+    # R products through gsm_apply, each pass timed with CUDA events on the
+    # plan's stream: first the right-preconditioned operator A M^-1 that the
+    # Krylov solves iterate with (three-component pass 1 with the scaled input
+    # written back, M^-1 x in pass 3: the kernels of the timed solves), then
+    # the plain Eq. 4 operator.  (Inside a solve, instances that have
+    # converged are masked, so a launch there moves less than B instances'
+    # bytes.)
     xd = torch.from_numpy(wl.random_field(N_HARM, 11, batch=B)).to(dev)
-    plan.apply(pts, xd, precision=gsm.FP32_REFINE)
-    plan.profile(True)
     R_MV = 5
-    torch.cuda.nvtx.range_push("roofline_product")   # lets ncu select these launches (--nvtx-include)
-    for _ in range(R_MV):
-        plan.apply(pts, xd, precision=gsm.FP32_REFINE)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    mvk = {name: plan.profile_get(k) for k, name in enumerate(["fwd_x", "yz_conv", "inv_x_green"])}
-    plan.profile(False)
-    n_mv = mvk["fwd_x"][0]
-    t_mv = sum(v[1] for v in mvk.values()) / max(1, n_mv) / 1000.0   # s per product
-    achieved = B * B_MV / t_mv / 1e9 if t_mv > 0 else 0.0
-    own = (B * OWN_MV + 4 * L_FFT ** 3) / t_mv / 1e9 if t_mv > 0 else 0.0
+
+    def product_roofline(precond, own_bytes, nvtx):
+        plan.apply(pts, xd, precision=gsm.FP32_REFINE, precond=precond)
+        plan.profile(True)
+        torch.cuda.nvtx.range_push(nvtx)   # lets ncu select these launches (--nvtx-include)
+        for _ in range(R_MV):
+            plan.apply(pts, xd, precision=gsm.FP32_REFINE, precond=precond)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        mvk = {name: plan.profile_get(k) for k, name in enumerate(["fwd_x", "yz_conv", "inv_x_green"])}
+        plan.profile(False)
+        n_mv = mvk["fwd_x"][0]
+        t_mv = sum(v[1] for v in mvk.values()) / max(1, n_mv) / 1000.0   # s per product
+        achieved = B * B_MV / t_mv / 1e9 if t_mv > 0 else 0.0
+        own = (B * own_bytes + 4 * L_FFT ** 3) / t_mv / 1e9 if t_mv > 0 else 0.0
+        traffic = NCU_TRAFFIC["precond" if precond else "plain"]
+        return {"kernel": "c64_product (%s + k_yz_t8x2 + k_inv_x_t8)" % ("k_fwd_x_t8h" if precond else "k_fwd_x_t8"),
+                "operator": "A M^-1 (as in the solves)" if precond else "A (Eq. 4)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind + " (copy, burst)", "traffic": traffic,
+                "algorithmic_bytes_per_launch": B * B_MV, "launches": n_mv, "avg_us": 1e6 * t_mv,
+                "passes_us": {k: 1000.0 * v[1] / max(1, v[0]) for k, v in mvk.items()},
+                "own_layout_bytes_per_launch": B * own_bytes + 4 * L_FFT ** 3,
+                "own_layout_GBps": own, "own_layout_frac": own / peak,
+                "traffic_over_own_layout": None if traffic is None else traffic / (B * own_bytes + 4 * L_FFT ** 3)}
+
+    roof = product_roofline(args.precond != "none", OWN_MV_PC if args.precond != "none" else OWN_MV,
+                            "roofline_product")
+    roof_plain = product_roofline(False, OWN_MV, "roofline_product_plain") if args.precond != "none" else None
     # Gram-Schmidt passes (dots + update) inside the profiled solve, at the
     # algorithmic bytes of the instances still iterating at each step
     kr_ms = kinds["krylov_dots"][1] + kinds["krylov_update"][1]
     kr_by = kinds["krylov_dots"][2] + kinds["krylov_update"][2]
     iters = [i["iters"] for i in infos]
     tot_ms = sum(v[1] for v in kinds.values())
+    # the whole solve: survey bytes of every product of every instance (B_mv
+    # per instance-product, twice that for the 16-byte certified residual)
+    # plus the Gram-Schmidt bytes, over the device time of one step
+    n_resid = sum(i["refine_steps"] for i in infos)
+    solve_bytes = (sum(iters) + 2 * n_resid) * B_MV + kr_by / args.steps
+    t_step = t_dev / args.steps
+    prof_by = sum(v[2] for v in kinds.values()) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec + c128 refinement", "data": "synthetic",
         "config": workload_config(args, ws),
         "fp64_plain": None if fp64_value is None else
-        {"value": fp64_value, "unit": "solves/s", "iters_mean": float(np.mean([i["iters"] for i in infos64]))},
+        {"value": fp64_value, "unit": "solves/s", "iters_mean": float(np.mean([i["iters"] for i in infos64])),
+         "roofline": fp64_roof},
+        "measured_fma_tflops": {"fp32": gsm.probe_fma(1, local, stream.cuda_stream),
+                                "fp32x2": gsm.probe_fma(2, local, stream.cuda_stream)},
         "speedup_vs_fp64": None if fp64_value is None else value / ws / fp64_value,
         "alt_krylov": alt_line,
         "iters_mean": float(np.mean(iters)), "refine_steps_mean": float(np.mean([i["refine_steps"] for i in infos])),
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
-        "roofline": {"kernel": "c64_product (k_fwd_x_t8 + k_yz_t8x2 + k_inv_x_t8)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind + " (copy, burst)", "traffic": NCU_TRAFFIC,
-                     "algorithmic_bytes_per_launch": B * B_MV, "launches": n_mv, "avg_us": 1e6 * t_mv,
-                     "passes_us": {k: 1000.0 * v[1] / max(1, v[0]) for k, v in mvk.items()},
-                     "own_layout_GBps": own, "own_layout_frac": own / peak},
+        "roofline": roof,
+        "roofline_plain_operator": roof_plain,
         "roofline_krylov": {"kernel": "k_dots + k_update", "bound": "hbm",
                             "achieved": kr_by / (kr_ms / 1000.0) / 1e9 if kr_ms > 0 else None,
                             "peak": peak, "unit": "GB/s",
                             "frac": (kr_by / (kr_ms / 1000.0) / 1e9) / peak if kr_ms > 0 else None,
                             "bytes": "active instances per step",
                             },
+        "roofline_solve": {"bytes_per_step": solve_bytes, "ms_per_step": 1000 * t_step,
+                           "achieved": solve_bytes / t_step / 1e9, "peak": peak, "unit": "GB/s",
+                           "frac": solve_bytes / t_step / 1e9 / peak,
+                           "bytes": "B_mv per instance-product (2 B_mv per certified residual) + Gram-Schmidt",
+                           "own_layout_GBps_profiled": prof_by / (1e-3 * tot_ms / args.steps) / 1e9 if tot_ms else None},
         "kernel_shares": {k: {"launches": v[0], "ms": v[1], "share": v[1] / tot_ms if tot_ms else None}
                           for k, v in kinds.items()},
         "profiled_ms_per_step": 1000 * t_prof / args.steps,

@@ -153,14 +153,21 @@ gsm_status gsm_set_permittivity(gsm_plan_t *plan, const double eps_host[2],
                                 const gsm_shape *shapes, int n_shapes,
                                 const double *voxel_eps, const int M[3]);
 
-/* y = A x (Eq. 4 operator, adjoint = 0) or y = A^H x (adjoint = 1) for n
- * points, each x/y of 3 N^3 complex128 (point's truncation).  on_device = 1:
- * x, y are device pointers; 0: host.  precision GSM_FP32_REFINE rounds x to
- * complex64 and applies the FP32 kernels (result widened to complex128);
- * GSM_DF64 applies the double-float kernels (adjoint = 0 and FFT sizes 32
- * or 64 only, else GSM_ERR_ARG). */
+/* y = op(A) x for n points, each x/y of 3 N^3 complex128 (point's
+ * truncation), A the plan's operator (Eq. 4, or Eq. 5 for a GSM_FORM_H plan):
+ *   op = 0: y = A x;
+ *   op = 1: y = A^H x (Eq. 4 only);
+ *   op = 2: y = A M^{-1} x, the right-preconditioned Eq. 4 operator that the
+ *           Krylov solves iterate with (GSM_PRECOND_AUTO above: lane-team
+ *           levels with |Delta_0| >= 1 and points that get s > 0, else
+ *           GSM_ERR_ARG), run by the same kernels as inside a solve.  Not in
+ *           the paper.
+ * on_device = 1: x, y are device pointers; 0: host.  precision
+ * GSM_FP32_REFINE rounds x to complex64 and applies the FP32 kernels (result
+ * widened to complex128); GSM_DF64 applies the double-float kernels (op = 0
+ * and FFT sizes 32 or 64 only, else GSM_ERR_ARG). */
 gsm_status gsm_apply(gsm_plan_t *plan, int n, const gsm_point *points,
-                     const double *x, double *y, int on_device, int precision, int adjoint);
+                     const double *x, double *y, int on_device, int precision, int op);
 
 /* Solve Eq. 4 for n points (any n; processed in batches of max_batch).  E
  * receives n fields of 3 N^3 complex128 (on_device selects device or host
@@ -215,8 +222,9 @@ gsm_status gsm_profile(gsm_plan_t *plan, int enable);
 gsm_status gsm_profile_get(gsm_plan_t *plan, int kind, long long *launches,
                            double *total_ms, double *bytes);
 
-/* y = A x (Eq. 4 operator, FP64 kernels) for ONE point at the plan's full
- * truncation, without allocating anything.  The paper has no counterpart:
+/* y = A x for ONE point at the plan's full truncation, with the plan's
+ * operator (Eq. 4, or Eq. 5 for a GSM_FORM_H plan) in FP64 kernels, without
+ * allocating anything.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc during a
  * solve step -- host applications whose own allocator has reserved the
  * device memory up front, or latency-critical loops in which the implicit
@@ -245,6 +253,15 @@ gsm_status gsm_tuned_blocks(const gsm_plan_t *plan, int precision, int blocks[3]
  * size 3 * 2^p, whichever ran one product of the batch faster when the level
  * was first built.  GSM_ERR_STATE if the level does not exist yet. */
 gsm_status gsm_level_fft(const gsm_plan_t *plan, const int n_harm[3], int fft_out[3]);
+
+/* Measured fused multiply-add throughput of `device` (no counterpart in the
+ * paper): the denominator of the arithmetic rooflines (FP64 product,
+ * double-float residual).  kind 0: FP64 FMA, 1: FP32 FMA, 2: packed FP32
+ * pairs (fma.rn.f32x2).  One wave of 256-thread blocks per SM slot, eight
+ * independent chains per thread, best of five launches timed with CUDA
+ * events on cuda_stream (NULL = default stream); *tflops = 2 x FMAs / s.
+ * Allocates and frees a small result buffer; changes no device setting. */
+gsm_status gsm_probe_fma(int device, void *cuda_stream, int kind, double *tflops);
 
 const char *gsm_last_error(const gsm_plan_t *plan);
 const char *gsm_version(void);

@@ -214,8 +214,12 @@ def optimise(args):
     t0 = time.perf_counter()
     v, hist = optimise_anisotropy(plan, vox, k0, win, steps=max(1, args.steps))
     dt = time.perf_counter() - t0
+    obj = hist[:, 0] - hist[:, 1]
+    acc = hist[:, 3] > 0
     print(json.dumps({"workload": "optimise eps_xx - eps_yy, 64^3 voxels, 21^3 harmonics",
-                      "steps": len(hist), "seconds": dt, "objective_first": float(hist[0][0] - hist[0][1]),
-                      "objective_last": float(hist[-1][0] - hist[-1][1]), "eps_last": list(map(float, hist[-1]))}),
+                      "evaluations": len(hist), "accepted": int(acc.sum()), "seconds": dt,
+                      "objective_first": float(obj[0]), "objective_best": float(obj[acc].max()),
+                      "objective": [round(float(o), 6) for o in obj], "accepted_flags": [int(a) for a in acc],
+                      "eps_history": [[round(float(e), 6) for e in h[:3]] for h in hist]}),
           flush=True)
     plan.close()

@@ -114,6 +114,7 @@ struct gsm_plan_s {
   bool team_only = false;  // GSM_FFT_PATH=team: shared-memory FFTs everywhere
   bool use_graphs = true;  // inner GMRES cycles as one graph launch (GSM_GRAPHS=0 disables)
   bool no_packed = false;  // GSM_PACKED=0: complex64 pass 2 one x plane per block instead of packed plane pairs
+  int yzv = 0;             // GSM_YZ=rot: complex64 pass 2 with lane-shuffle transposes (k_yz_t8x2r)
   cudaStream_t cap_st = nullptr;  // private stream used only to capture graphs
   // pinned host staging
   char *pin = nullptr;
@@ -634,8 +635,11 @@ static cudaError_t matvec(gsm_plan_t *p, const Level &lv, const MatvecArgs<R> &a
   } else {
     // the lane-team kernels take the forward and residual forms of both
     // equations and the adjoint forms of Eq. 4
-    if (!p->team_only && (a.mode < 2 || a.form == 0) && reg_path_ok(a.g))
-      return launch_matvec_reg<R>(a, st, prof, lv.tb[sizeof(R) == 4 ? 1 : 0]);
+    if (!p->team_only && (a.mode < 2 || a.form == 0) && reg_path_ok(a.g)) {
+      MatvecArgs<R> b = a;
+      b.yzv = p->yzv;
+      return launch_matvec_reg<R>(b, st, prof, lv.tb[sizeof(R) == 4 ? 1 : 0]);
+    }
     if (a.pc) return cudaErrorInvalidValue;   // the preconditioned product exists only on the lane-team path
     return launch_matvec<R>(a, st, prof);
   }
@@ -662,6 +666,7 @@ static cudaError_t autotune(gsm_plan_t *p, Level &lv, const MatvecArgs<R> &base)
     }
   }
   MatvecArgs<R> a = base;
+  a.yzv = p->yzv;
   a.scale = nullptr;
   a.write_back = 0;
   a.act = nullptr;
@@ -1093,6 +1098,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
         }
         mv.X = V + (long long)j * Us;
         mv.Y = V + (long long)(j + 1) * Us;
+        mv.nact = prof ? k.nact : 0;
         CK(matvec<R>(p, lv, mv, prof));
         CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
         CK(launch_finish(k, j, st));
@@ -1134,6 +1140,8 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       md.write_back = 0;
       md.mode = adj ? 2 : 0;
       md.act = w->need;
+      md.nact = 0;
+      for (int b = 0; b < B; ++b) md.nact += need[b] != 0;
       CK(matvec<R>(p, lv, md, prof));
       CK(launch_resid_sub(w->r64, g.U, (const float2 *)V, vinst, g.U, B, k.nblk, w->need, w->mv_partial,
                           w->mv_counter, w->mv_norm, st));
@@ -1280,6 +1288,8 @@ gsm_status gsm_plan(const gsm_plan_desc *desc, gsm_plan_t **out) {
     p->use_graphs = !(gr && std::strcmp(gr, "0") == 0);
     const char *pk = std::getenv("GSM_PACKED");
     p->no_packed = pk && std::strcmp(pk, "0") == 0;
+    const char *yz = std::getenv("GSM_YZ");
+    p->yzv = (yz && std::strcmp(yz, "rot") == 0) ? 1 : 0;
   }
   std::vector<double2> t64(TWN_HOST);
   std::vector<float2> t32(TWN_HOST);
@@ -1397,17 +1407,42 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     return fail(p, GSM_ERR_ARG, "gsm_apply: unknown precision");
   if (precision == GSM_DF64 && (adjoint || p->team_only || !reg_path_ok(g) || !lv->Ddf))
     return fail(p, GSM_ERR_ARG, "gsm_apply: the double-float product needs FFT sizes 32/64 and adjoint = 0");
-  if (adjoint && p->d.form != GSM_FORM_E) return fail(p, GSM_ERR_ARG, "gsm_apply: the adjoint exists for the E-field form");
+  if (adjoint < 0 || adjoint > 2) return fail(p, GSM_ERR_ARG, "gsm_apply: operator must be 0 (A), 1 (A^H) or 2 (A M^-1)");
+  if (adjoint && p->d.form != GSM_FORM_E)
+    return fail(p, GSM_ERR_ARG, "gsm_apply: the adjoint and the preconditioned operator exist for the E-field form");
+  // op 2: A M^{-1} x with the right preconditioner of the Krylov solves, run
+  // exactly as inside a solve (three-component pass 1 that also writes the
+  // scaled input back, M^{-1} x in the identity term of pass 3)
+  const bool pcop = adjoint == 2;
+  if (pcop && (precision == GSM_DF64 || p->team_only || !reg_path_ok(g) || !(std::fabs(lv->delta0) >= 1.0)))
+    return fail(p, GSM_ERR_ARG,
+                "gsm_apply: the preconditioned operator needs a lane-team level with |Delta_0| >= 1 (FP64 or FP32)");
   const int prec = precision == GSM_FP32_REFINE;
   Work *w;
   if ((s = get_work(p, g, n, 2, 0, &w))) return s;
-  if ((s = ensure_pinned(p, (size_t)n * sizeof(Inst)))) return s;
+  if ((s = ensure_pinned(p, (size_t)n * (sizeof(Inst) + 12)))) return s;
   Inst *hI = (Inst *)p->pin;
-  for (int b = 0; b < n; ++b)
+  for (int b = 0; b < n; ++b) {
     if ((s = make_inst(p, points[b], g, hI[b]))) return s;
+    if (pcop) {
+      set_precond(hI[b], g, lv->delta0);
+      if (hI[b].pc_c == 0.0) return fail(p, GSM_ERR_ARG, "gsm_apply: no preconditioner for this point (s = 0)");
+    }
+  }
   cudaStream_t st = p->st;
   CK(cudaMemcpyAsync(w->inst, hI, n * sizeof(Inst), cudaMemcpyHostToDevice, st));
   CK(launch_iden(g, w->inst, n, w->iden64, w->iden32, st, w->idendf));
+  if (pcop) {
+    // unit scales of the write-back (the solve's scales normalise Krylov vectors)
+    double *h64 = reinterpret_cast<double *>(hI + n);
+    float *h32 = reinterpret_cast<float *>(h64 + n);
+    for (int b = 0; b < n; ++b) {
+      h64[b] = 1.0;
+      h32[b] = 1.0f;
+    }
+    CK(cudaMemcpyAsync(w->k.scale64, h64, n * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w->k.scale32, h32, n * 4, cudaMemcpyHostToDevice, st));
+  }
   const size_t bytes = (size_t)n * g.U * 16;
   double2 *xd = w->x64, *yd = w->r64;
   CK(cudaMemcpyAsync(xd, x, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -1428,8 +1463,13 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.inst = w->inst;
     a.iden = w->iden32;
     a.tw = p->tw32;
-    a.mode = adjoint ? 2 : 0;
+    a.mode = adjoint == 1 ? 2 : 0;
     a.form = p->d.form;
+    if (pcop) {
+      a.pc = 1;
+      a.write_back = 1;
+      a.scale = w->k.scale32;
+    }
     CK(matvec<float>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
     CK(launch_convert_f2d(yf, yd, (long long)n * g.U, st));
   } else if (precision == GSM_DF64) {
@@ -1461,8 +1501,13 @@ gsm_status gsm_apply(gsm_plan_t *p, int n, const gsm_point *points, const double
     a.inst = w->inst;
     a.iden = w->iden64;
     a.tw = p->tw64;
-    a.mode = adjoint ? 2 : 0;
+    a.mode = adjoint == 1 ? 2 : 0;
     a.form = p->d.form;
+    if (pcop) {
+      a.pc = 1;
+      a.write_back = 1;
+      a.scale = w->k.scale64;
+    }
     CK(matvec<double>(p, *lv, a, p->prof.on ? &p->prof : nullptr));
   }
   CK(cudaMemcpyAsync(y, yd, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));

@@ -184,3 +184,97 @@ struct Team8x2 {
 };
 
 }  // namespace gsm
+
+namespace gsm {
+
+// The same 64-point transforms of two planes at once, with the transpose
+// between the two radix-8 stages done by lane shuffles instead of the team
+// buffer.  With w = exp(S 2 pi i / 64), w8 = w^8 and X[p + 8 s] =
+// sum_t w^{t p} w8^{t s} Y[t][p], Y[t][p] = sum_a x[t + 8 a] w8^{a p}:
+//
+// forward<S> (lane t holds x[t + 8 a] in register a):
+//   1. u[a] = x[t + 8 a] w8^{a t}; the DFT over a then gives register r the
+//      value Y[t][(r + t) mod 8] (a rotation by the lane index);
+//   2. twiddle register r by w^{t ((r + t) mod 8)};
+//   3. round k = 1..7: register k takes register k of lane (t - k) mod 8,
+//      which holds Y'[(t - k) mod 8][t]: one shuffle per round, the same
+//      register on both sides (register 0 keeps Y'[t][t]);
+//   4. X[t + 8 s] = w8^{t s} sum_k w8^{-k s} R[k]: a DFT of sign -S over k.
+//      The factor w8^{t s} is NOT applied: register s returns
+//      Z[s] = X[t + 8 s] w8^{-t s} ("phase-deferred" spectral layout).
+// inverse<S'> (lane p holds, in register s, X[p + 8 s] w8'^{p s} with
+// w8' = exp(S' 2 pi i / 8)): a DFT of sign S' over s gives W[p][(r + p) mod 8]
+// directly (the modulation is the input's), twiddle w'^{p ((r + p) mod 8)},
+// the same seven shuffle rounds, a DFT of sign -S' over k, and x[t + 8 a] =
+// w8'^{a t} Q[a] for the kept outputs a in {0, 1, 6, 7}.
+//
+// For S' = -S the phase-deferred output of forward<S> is exactly the input
+// inverse<S'> expects: a pointwise real multiplier between them (D along z)
+// and any factor constant along a transform (the y phases are constant
+// along each z column, which the z convolution carries linearly) leave the
+// pair forward<+1> ... inverse<-1> equal to the plain transforms.
+struct Team8x2R {
+  static constexpr int L = 64;
+
+  // per lane t: tw[r] = w^{t ((r + t) mod 8)} (r < 8) and md[j] = w8^{a t}
+  // for a = 1, 6, 7 (j = 0, 1, 2), from the positive-sign table
+  __device__ static __forceinline__ void constants(WP (&tw)[8], WP (&md)[3], int t, const float2 *twg) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const float2 x = __ldg(&twg[((t * ((r + t) & 7)) & 63) * (TWN / L)]);
+      tw[r].c = make_float2(x.x, x.x);
+      tw[r].s = make_float2(x.y, x.y);
+    }
+    const int as[3] = {1, 6, 7};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float2 x = __ldg(&twg[((8 * as[j] * t) & 63) * (TWN / L)]);
+      md[j].c = make_float2(x.x, x.x);
+      md[j].s = make_float2(x.y, x.y);
+    }
+  }
+
+  // register k <- register k of team lane (t - k) mod 8, k = 1..7
+  __device__ static __forceinline__ void rotate_exchange(CP (&v)[8], int t, unsigned mask) {
+    const int base = (threadIdx.x & 31) & ~7;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      const int src = base | ((t - k) & 7);
+      v[k].re.x = __shfl_sync(mask, v[k].re.x, src);
+      v[k].re.y = __shfl_sync(mask, v[k].re.y, src);
+      v[k].im.x = __shfl_sync(mask, v[k].im.x, src);
+      v[k].im.y = __shfl_sync(mask, v[k].im.y, src);
+    }
+  }
+
+  // forward of inputs whose registers 2..5 are zero; phase-deferred output
+  template <int S>
+  __device__ static __forceinline__ void forward(CP (&v)[8], int t, const WP (&tw)[8], const WP (&md)[3],
+                                                 unsigned mask) {
+    v[1] = cp_twiddle<S>(v[1], md[0]);
+    v[6] = cp_twiddle<S>(v[6], md[1]);
+    v[7] = cp_twiddle<S>(v[7], md[2]);
+    Team8x2::dft8_in0167<S>(v);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = cp_twiddle<S>(v[r], tw[r]);
+    rotate_exchange(v, t, mask);
+    Team8x2::dft8<-S>(v);
+  }
+
+  // inverse of a phase-deferred input; natural outputs at a in {0, 1, 6, 7}
+  // only (the others are left undefined)
+  template <int S>
+  __device__ static __forceinline__ void inverse(CP (&v)[8], int t, const WP (&tw)[8], const WP (&md)[3],
+                                                 unsigned mask) {
+    Team8x2::dft8<S>(v);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = cp_twiddle<S>(v[r], tw[r]);
+    rotate_exchange(v, t, mask);
+    Team8x2::dft8_out0167<-S>(v);
+    v[1] = cp_twiddle<S>(v[1], md[0]);
+    v[6] = cp_twiddle<S>(v[6], md[1]);
+    v[7] = cp_twiddle<S>(v[7], md[2]);
+  }
+};
+
+}  // namespace gsm

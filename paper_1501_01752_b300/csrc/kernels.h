@@ -95,6 +95,9 @@ template <typename R> struct MatvecArgs {
   double *norm_out = nullptr;  // ||Y||^2 per instance (nullptr = skip)
   const int *jdev = nullptr;   // graph mode: X and Y advance by (*jdev) * jstride
   long long jstride = 0;
+  int nact = 0;                // profiling only: instances still active (0 = all B), for the byte count
+  int yzv = 0;                 // complex64 pass 2: 1 = lane-shuffle transposes (k_yz_t8x2r),
+                               // 0 = team-buffer transposes (k_yz_t8x2)
 };
 
 template <typename R> cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *prof);
@@ -129,8 +132,11 @@ struct KrylovPtrs {
   long long U;              // logical vector length (3 N^3)
   long long Us;             // stored stride: U rounded up to 64 (pads stay zero)
   int nblk;                 // blocks per instance for vector kernels
-  int bcap;                 // most blocks per instance (one 2048-element tile each): the
-                            // Gram-Schmidt passes spread nblk * B blocks over the active instances
+  int bcap;                 // most blocks per instance, one per 2048 elements: the Gram-Schmidt
+                            // passes spread nblk * B blocks over the active instances.  2048 is the
+                            // FP32 update's tile; k_dots tiles hold 1024 (FP32) or 512 (FP64)
+                            // elements and the FP64 update's 1024, so there a lone instance gets
+                            // fewer blocks than tiles and each block loops over several tiles
   int *alist;               // [B + 1]: number of active instances, then their indices
   double *partial;          // [B][nblk][2(m+1)+1]
   unsigned *counter;        // [B]

@@ -472,6 +472,103 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, c
 
 
 
+// Pass 2 as k_yz_t8x2 with the transposes inside each 64-point transform done
+// by lane shuffles (Team8x2R) instead of team buffers: shared memory holds
+// only the plane.  The y forward leaves its rows phase-deferred (frequency
+// r_y carries the factor w8^{-(r_y mod 8)(r_y / 8)}, constant along each z
+// column); the z forward, x D, z inverse of a column keep that factor, and
+// the y inverse consumes it, so T is left exactly as by k_yz_t8x2.
+template <int TT>
+__global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, const float2 *__restrict__ Dp,
+                                                 const int *__restrict__ act, const float2 *__restrict__ twg) {
+  using F = Team8x2R;
+  constexpr int NT = TT / 8;
+  extern __shared__ __align__(16) unsigned char sm_dyn[];
+  CP *A = reinterpret_cast<CP *>(sm_dyn);   // [N2][YZP] value pairs
+  const int N1 = g.N[1], N2 = g.N[2];
+  const int xp = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
+  if (act && !act[b]) return;
+  float2 *Ta = T + b * g.Tsz + ((long long)(2 * xp) * 3 + c) * N2 * N1;   // [m_z][m_y] block of r_x = 2 xp
+  float2 *Tb = Ta + 3LL * N2 * N1;                                         // and of r_x = 2 xp + 1
+  const int team = threadIdx.x >> 3, lane = threadIdx.x & 7;
+  const unsigned mask = 0xffu << (threadIdx.x & 24);
+  WP tw[8], md[3];
+  F::constants(tw, md, lane, twg);
+  int hy[4], hz[4];   // harmonic held by register reg0167(k) of this lane along y / z, or -1
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    hy[k] = harm_at(lane + 8 * reg0167(k), g.n[1], 64);
+    hz[k] = harm_at(lane + 8 * reg0167(k), g.n[2], 64);
+  }
+  const CP zero = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  // y forward: team per m_z row of both planes, straight from global memory
+  for (int r0 = 0; r0 < N2; r0 += NT) {
+    const int mz = r0 + team;
+    const bool valid = mz < N2;
+    const float2 *ra = Ta + mz * N1, *rb = Tb + mz * N1;
+    CP v[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) v[a] = zero;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (valid && hy[k] >= 0) {
+        const float2 xa = ra[hy[k]], xb = rb[hy[k]];
+        v[reg0167(k)] = {make_float2(xa.x, xb.x), make_float2(xa.y, xb.y)};
+      }
+    F::forward<+1>(v, lane, tw, md, mask);
+    if (valid) {
+      CP *Ar = A + mz * YZP + lane;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) Ar[8 * q] = v[q];
+    }
+  }
+  __syncthreads();
+  // z forward, times D, z inverse: team per y-frequency column
+  const float2 *Dx = Dp + (long long)xp * 64 * 64;
+  for (int c0 = 0; c0 < 64; c0 += NT) {
+    const int ry = c0 + team;
+    CP v[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) v[a] = zero;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (hz[k] >= 0) v[reg0167(k)] = A[hz[k] * YZP + ry];
+    F::forward<+1>(v, lane, tw, md, mask);
+    const float2 *Dc = Dx + ry * 64 + lane;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 d = __ldg(&Dc[8 * q]);
+      v[q].re = f2::mul(v[q].re, d);
+      v[q].im = f2::mul(v[q].im, d);
+    }
+    F::inverse<-1>(v, lane, tw, md, mask);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (hz[k] >= 0) A[hz[k] * YZP + ry] = v[reg0167(k)];
+  }
+  __syncthreads();
+  // y inverse: team per row, straight to global memory
+  for (int r0 = 0; r0 < N2; r0 += NT) {
+    const int mz = r0 + team;
+    const bool valid = mz < N2;
+    CP v[8];
+    const CP *Ar = A + mz * YZP + lane;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = valid ? Ar[8 * q] : zero;
+    F::inverse<-1>(v, lane, tw, md, mask);
+    if (valid) {
+      float2 *ra = Ta + mz * N1, *rb = Tb + mz * N1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (hy[k] >= 0) {
+          const CP x = v[reg0167(k)];
+          ra[hy[k]] = make_float2(x.re.x, x.im.x);
+          rb[hy[k]] = make_float2(x.re.y, x.im.y);
+        }
+    }
+  }
+}
+
 // MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u); HF = 1 (Eq. 5): G u is
 // replaced by k_m x u / (k_m^2 - k_b^2).  nog = 1 (adjoint of Eq. 4, G
 // already applied in pass 1): G u is replaced by u.
@@ -702,6 +799,13 @@ static void pass2(const MatvecArgs<R> &a, cudaStream_t st) {
   using C = typename Cx<R>::T;
   const Geo &g = a.g;
   if constexpr (sizeof(R) == 4) {
+    if (a.Dp && packed_yz_ok(g) && a.yzv == 1) {
+      const size_t smem2 = sizeof(CP) * (size_t)g.N[2] * YZP;
+      dim3 grid2(g.L[0] / 2, 3, a.B);
+      cudaFuncSetAttribute(k_yz_t8x2r<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+      k_yz_t8x2r<TT><<<grid2, TT, smem2, st>>>(g, a.T, a.Dp, a.act, a.tw);
+      return;
+    }
     if (a.Dp && packed_yz_ok(g)) {
       const size_t smem2 = sizeof(CP) * ((size_t)g.N[2] * YZP + (TT / 8) * Team8x2::BUF);
       dim3 grid2(g.L[0] / 2, 3, a.B);
@@ -813,13 +917,20 @@ cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler 
   cudaError_t e;
   if (prof) prof->begin(KIND_FWD_X, st);
   if ((e = launch_reg_pass<R>(1, t1, a, st)) != cudaSuccess) return e;
-  if (prof) prof->end(KIND_FWD_X, st, (double)a.B * cs * (double)(g.U + g.Tsz));
+  // bytes this layout moves per launch, for the instances still active: pass 1
+  // reads x and writes T (plus the scaled x written back inside solves and,
+  // in the three-component variant, the per-harmonic denominators)
+  const double nb = a.nact > 0 ? a.nact : a.B;
+  const bool p1h = a.form || a.pc || a.mode >= 2;
+  if (prof)
+    prof->end(KIND_FWD_X, st,
+              nb * (cs * (double)(g.U + g.Tsz + (a.write_back ? g.U : 0)) + (p1h ? sizeof(R) * (double)g.Nh : 0.0)));
   if (prof) prof->begin(KIND_YZ, st);
   if ((e = launch_reg_pass<R>(2, t2, a, st)) != cudaSuccess) return e;
-  if (prof) prof->end(KIND_YZ, st, (double)a.B * 2.0 * cs * (double)g.Tsz + sizeof(R) * (double)g.L[0] * g.L[1] * g.L[2]);
+  if (prof) prof->end(KIND_YZ, st, nb * 2.0 * cs * (double)g.Tsz + sizeof(R) * (double)g.L[0] * g.L[1] * g.L[2]);
   if (prof) prof->begin(KIND_INV_X, st);
   if ((e = launch_reg_pass<R>(3, t3, a, st)) != cudaSuccess) return e;
-  if (prof) prof->end(KIND_INV_X, st, (double)a.B * (cs * (double)(g.Tsz + 2 * g.U) + sizeof(R) * (double)g.Nh));
+  if (prof) prof->end(KIND_INV_X, st, nb * (cs * (double)(g.Tsz + 2 * g.U) + sizeof(R) * (double)g.Nh));
   return cudaGetLastError();
 }
 

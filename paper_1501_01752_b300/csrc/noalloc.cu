@@ -1,6 +1,7 @@
-// gsm_apply_noalloc: the FP64 Eq. 4 matrix-vector product for one point
-// with every temporary in one fixed device array, for callers that must not
-// allocate device memory during the call (see include/gsm.h).
+// gsm_apply_noalloc: the FP64 matrix-vector product of the plan's operator
+// (Eq. 4, or Eq. 5 for an H-field plan) for one point with every temporary in
+// one fixed device array, for callers that must not allocate device memory
+// during the call (see include/gsm.h).
 #include <cuda_runtime.h>
 
 #include <mutex>

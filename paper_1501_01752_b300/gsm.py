@@ -82,6 +82,7 @@ def _load():
         "gsm_tuned_blocks": (ct.c_int, [P, ct.c_int, ct.POINTER(ct.c_int)]),
         "gsm_level_fft": (ct.c_int, [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
         "gsm_profile_get": (ct.c_int, [P, ct.c_int, ct.POINTER(ct.c_longlong), dp, dp]),
+        "gsm_probe_fma": (ct.c_int, [ct.c_int, P, ct.c_int, dp]),
         "gsm_last_error": (ct.c_char_p, [P]),
         "gsm_version": (ct.c_char_p, []),
     }
@@ -141,6 +142,16 @@ def fit_poles(kappa, xi, Np=5, Nd=10):
     if s:
         raise GsmError(s, "gsm_fit_poles")
     return eta.view(np.complex128), zeta.view(np.complex128)
+
+
+def probe_fma(kind, device=0, stream=None):
+    """Measured FMA throughput in TFLOP/s (gsm_probe_fma): kind 0 FP64,
+    1 FP32, 2 packed FP32 pairs."""
+    out = ct.c_double()
+    s = lib.gsm_probe_fma(device, stream, kind, ct.byref(out))
+    if s:
+        raise GsmError(s, "gsm_probe_fma")
+    return out.value
 
 
 def plan_query(periods, n_harm, precision=FP32_REFINE, fft=(0, 0, 0), max_batch=0, restart=0, hbm_cap=0):
@@ -239,9 +250,12 @@ class Plan:
             N = point["n_harm"]
         return 3 * N[0] * N[1] * N[2]
 
-    def apply(self, points, x, precision=FP64, adjoint=False):
-        """y = A x (or A^H x) for n points; x of shape (n, 3, Nz, Ny, Nx)
-        complex128, numpy (host) or torch CUDA tensor (device)."""
+    def apply(self, points, x, precision=FP64, adjoint=False, precond=False):
+        """y = A x (A^H x with adjoint, A M^{-1} x with precond: the right-
+        preconditioned operator of the Krylov solves) for n points; x of shape
+        (n, 3, Nz, Ny, Nx) complex128, numpy (host) or torch CUDA tensor
+        (device)."""
+        op = 2 if precond else int(bool(adjoint))
         pts = make_points(points)
         dev = not isinstance(x, np.ndarray)
         if dev:
@@ -249,12 +263,12 @@ class Plan:
             xin = x.contiguous()
             y = torch.empty_like(xin)
             s = lib.gsm_apply(self.h, len(points), pts, ct.c_void_p(xin.data_ptr()), ct.c_void_p(y.data_ptr()), 1,
-                              precision, int(adjoint))
+                              precision, op)
         else:
             xin = np.ascontiguousarray(x, dtype=np.complex128)
             y = np.empty_like(xin)
             s = lib.gsm_apply(self.h, len(points), pts, ct.c_void_p(xin.ctypes.data), ct.c_void_p(y.ctypes.data), 0,
-                              precision, int(adjoint))
+                              precision, op)
         self._check(s, "gsm_apply")
         return y
 

@@ -111,3 +111,37 @@ def test_preconditioned_128_point_teams_gyroid():
         assert np.linalg.norm(r) / np.linalg.norm(rhs) < 1.2e-8
         assert rel(res[g.PRECOND_AUTO][0][b], res[g.PRECOND_NONE][0][b]) < 2e-6
     assert res[g.PRECOND_AUTO][1] < res[g.PRECOND_NONE][1], (res[g.PRECOND_AUTO][1], res[g.PRECOND_NONE][1])
+
+
+@pytest.mark.parametrize("n_harm", [N15, (31, 31, 31)])
+def test_preconditioned_operator_matches_oracle(n_harm):
+    # gsm_apply op 2 (the product the solves iterate with) against the
+    # oracle's Eq. 4 operator applied to M^{-1} x, M = I - Delta_0 G(m)
+    # inverted here as an explicit 3 x 3 matrix per harmonic; the points are
+    # chosen where the largest scale s = 1 qualifies (checked below)
+    from oracle import operator as oop
+    g = gsm()
+    st = wl.woodpile()
+    ost = oracle_structure(st)
+    Delta = ost.delta(n_harm, 1.0)
+    d0 = Delta[tuple(s // 2 for s in Delta.shape)].real
+    pts = [wl.point(0.8 * K0), wl.point(0.72 * K0, (0, 0, 1), (0, 1, 0)),
+           wl.point(0.75 * K0, (0.6, 0.0, 0.8), (0.0, 1.0, 0.0))]
+    x = wl.random_field(n_harm, 77, batch=len(pts))
+    plan = g.plan_for(st, n_harm, precision=g.FP64)
+    y64 = plan.apply(pts, x, precision=g.FP64, precond=True)
+    y32 = plan.apply(pts, x, precision=g.FP32_REFINE, precond=True)
+    for b, pt in enumerate(pts):
+        kinc = pt["kappa"] * np.asarray(pt["kdir"])
+        kb2 = pt["k0"] ** 2
+        kx, ky, kz = oop.wavevectors(n_harm, kinc, st["periods"])
+        KZ, KY, KX = np.meshgrid(kz, ky, kx, indexing="ij")
+        k2 = KX ** 2 + KY ** 2 + KZ ** 2
+        assert np.min(np.abs(k2 - kb2 * (1 + d0))) >= 0.1 * abs(d0) * kb2   # s = 1 qualifies
+        G = oop.green(n_harm, kinc, st["periods"], kb2)
+        Minv = np.linalg.inv(np.eye(3) - d0 * G)
+        u = np.einsum("zyxab,bzyx->azyx", Minv, x[b])
+        want = oop.Operator(Delta, n_harm, kinc, st["periods"], kb2)(u)
+        assert rel(y64[b], want) < 1e-12, (b, rel(y64[b], want))
+        assert rel(y32[b], want) < 1e-5, (b, rel(y32[b], want))
+    plan.close()

@@ -83,7 +83,9 @@ def test_woodpile_31_full_size(prec):
     n_harm = (31, 31, 31)
     pts = wl.woodpile_batch(4)
     fp64 = prec == "fp64"
-    plan = g.plan_for(st, n_harm, precision=g.FP64 if fp64 else g.FP32_REFINE, tol=1e-11 if fp64 else 1e-8)
+    # FP64 mode solves to 1e-13 so that the field parity holds at 1e-10
+    # (field error <= cond(A) x residual); refined mode to the bench's 1e-8
+    plan = g.plan_for(st, n_harm, precision=g.FP64 if fp64 else g.FP32_REFINE, tol=1e-13 if fp64 else 1e-8)
     E, infos, s = plan.solve(pts)
     assert s == 0
     ost = oracle_structure(st)
@@ -94,10 +96,10 @@ def test_woodpile_31_full_size(prec):
         A = oop.Operator(Delta, n_harm, kinc, st["periods"], p["k0"] ** 2)
         bvec = oop.incident(p["pol"], n_harm)
         res = np.linalg.norm(bvec - A(Eb)) / np.linalg.norm(bvec)   # oracle's own residual of the GPU field
-        assert res <= (1.5e-11 if fp64 else 1.5e-8), (b, res)
+        assert res <= (1.5e-13 if fp64 else 1.5e-8), (b, res)
         if b < 2:
-            want = _oracle_solve(st, n_harm, 1.0, p, method="gmres", tol=1e-12)
-            assert rel(Eb, want) < (1e-9 if fp64 else 1e-6), (b, rel(Eb, want))
+            want = _oracle_solve(st, n_harm, 1.0, p, method="gmres", tol=1e-13)
+            assert rel(Eb, want) < (1e-10 if fp64 else 1e-6), (b, rel(Eb, want))
     plan.close()
 
 
@@ -202,4 +204,38 @@ def test_new_permittivity_rebuilds_captured_cycles(krylov, monkeypatch):
         E2, _, s2 = fresh.solve(pts)
         fresh.close()
         assert s == 0 and s2 == 0 and rel(E, E2) < 1e-12, rel(E, E2)
+    plan.close()
+
+
+def test_one_slow_instance_in_a_batch_of_512(monkeypatch):
+    # the Gram-Schmidt passes give the instances still iterating all the
+    # blocks of the batch (device-side active list): with 511 fast points
+    # and one slow one, the long tail of the slow instance runs with a
+    # single active instance inside the captured WHILE cycles (every other
+    # block returns at once).  Its iterations and field must match a solve of
+    # that point alone, and a second solve on the same workspace (counters
+    # left by the first) must reproduce the first bit for bit.
+    monkeypatch.setenv("GSM_BLOCKS", "256,256,256")
+    g = gsm()
+    st = wl.woodpile()
+    n_harm = (15, 15, 15)
+    easy = wl.point(0.75 * K0)
+    slow = wl.point(np.sqrt(3.725) * 1.001 * K0)   # just above the averaged medium's light cone
+    pts = [easy] * 512
+    pts[300] = slow
+    plan = g.plan_for(st, n_harm, precision=g.FP32_REFINE, tol=1e-8, max_batch=512)
+    E1, inf1, s1 = plan.solve(pts)
+    E2, inf2, s2 = plan.solve(pts)
+    assert s1 == 0 and s2 == 0
+    assert np.array_equal(E1, E2) and [i["iters"] for i in inf1] == [i["iters"] for i in inf2]
+    it = [i["iters"] for i in inf1]
+    assert it[300] > max(it[:300] + it[301:]), it[300]
+    assert all(i["rel_residual"] <= 1e-8 for i in inf1)
+    alone = g.plan_for(st, n_harm, precision=g.FP32_REFINE, tol=1e-8, max_batch=1)
+    Ea, infa, sa = alone.solve([slow])
+    alone.close()
+    assert sa == 0 and abs(infa[0]["iters"] - it[300]) <= 2, (infa, inf1[300])
+    assert rel(E1.reshape(512, -1)[300], Ea.ravel()) < 1e-6
+    want = _oracle_solve(st, n_harm, 1.0, slow, method="gmres", tol=1e-12)
+    assert rel(E1.reshape(512, -1)[300], want.ravel()) < 1e-6
     plan.close()
