@@ -43,17 +43,16 @@ B_MV = 8 * 3 * (2 * N_HARM[0] ** 3 + 4 * L_FFT ** 2 * N_HARM[0]) + 4 * L_FFT ** 
 # product (3 L N^2 intermediate): x-forward s_c (U + 3 L N^2), yz pass
 # 2 s_c 3 L N^2, x-inverse + Green s_c (3 L N^2 + 2 U) + 4 N^3, plus the
 # multiplier once per launch.  The preconditioned product of the solves adds
-# the scaled input written back by pass 1 (s_c U) and the per-harmonic
-# denominators read by its three-component pass 1 (4 N^3).
+# the per-harmonic denominators read by its three-component pass 1 (4 N^3).
 _U = 3 * N_HARM[0] ** 3
 _TSZ = 3 * L_FFT * N_HARM[1] * N_HARM[2]
 OWN_MV = 8 * (_U + _TSZ) + 16 * _TSZ + 8 * (_TSZ + 2 * _U) + 4 * N_HARM[0] ** 3
-OWN_MV_PC = OWN_MV + 8 * _U + 4 * N_HARM[0] ** 3
+OWN_MV_PC = OWN_MV + 4 * N_HARM[0] ** 3
 # dram__bytes_read.sum + dram__bytes_write.sum of the three kernels of one
 # product launch at the bench batch (512 instances), from one ncu capture of
 # the current kernels, per operator; None where no capture of the current
 # kernels exists.
-NCU_TRAFFIC = {"precond": 4.5105e9, "plain": 4.0812e9}
+NCU_TRAFFIC = {"precond": None, "plain": None}
 # FP64 work of one FP64 product of one instance on this grid, from one ncu
 # count of the three FP64 product kernels at 32 instances: floating-point
 # operations (2 DFMA + DADD + DMUL) and FP64-pipe instructions (DFMA + DADD +
@@ -211,7 +210,7 @@ def main():
     ap.add_argument("--sweep-batch", type=int, default=128,
                     help="instances per launch of the sweep workload (points are grouped by truncation)")
     ap.add_argument("--workload", default="woodpile",
-                    choices=["woodpile", "matvec", "sweep", "gyroid", "adjoint", "optimise"])
+                    choices=["woodpile", "matvec", "sweep", "gyroid", "adjoint", "optimise", "nearpole"])
     args = ap.parse_args()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -382,7 +381,7 @@ def main():
         achieved = B * B_MV / t_mv / 1e9 if t_mv > 0 else 0.0
         own = (B * own_bytes + 4 * L_FFT ** 3) / t_mv / 1e9 if t_mv > 0 else 0.0
         traffic = NCU_TRAFFIC["precond" if precond else "plain"]
-        return {"kernel": "c64_product (%s + k_yz_t8x2 + k_inv_x_t8)" % ("k_fwd_x_t8h" if precond else "k_fwd_x_t8"),
+        return {"kernel": "c64_product (%s + k_yz_t8x2r + k_inv_x_t8)" % ("k_fwd_x_t8h" if precond else "k_fwd_x_t8"),
                 "operator": "A M^-1 (as in the solves)" if precond else "A (Eq. 4)",
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind + " (copy, burst)", "traffic": traffic,

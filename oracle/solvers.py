@@ -128,3 +128,61 @@ def bicgstab(apply, b, tol=1e-10, max_iter=2000):
     rel = np.linalg.norm(b - A(x)) / bnorm
     return x.reshape(shape), dict(iters=it, rel_residual=rel, history=history,
                                   converged=bool(rel <= tol))
+
+
+def minres(apply_h, c, precond=None, tol=1e-10, max_iter=2000):
+    """Preconditioned MINRES (Paige and Saunders) for a Hermitian, possibly
+    indefinite H: minimises ||c - H x|| in the norm of precond^{-1} over the
+    Krylov space of precond^{-1} H, with a three-term Lanczos recurrence (real
+    coefficients for Hermitian H) and Givens rotations.  precond(r) applies
+    M^{-1} of a Hermitian positive definite M (None = identity).  Stops when
+    the recurrence's residual estimate phibar falls to tol * beta1.
+
+    Used for the Hermitian form of the lossless Eq. 4 (G^{-1} - Delta) E =
+    G^{-1} E_inc, a Krylov variant the paper does not use; returns (x, info)
+    as gmres does, with iters = products with H."""
+    c = np.asarray(c, complex)
+    shape = c.shape
+    c = c.ravel()
+    H = lambda v: np.asarray(apply_h(v.reshape(shape))).ravel()
+    Mi = (lambda v: v) if precond is None else (lambda v: np.asarray(precond(v.reshape(shape))).ravel())
+    x = np.zeros_like(c)
+    r1 = c.copy()
+    y = Mi(r1)
+    beta1 = np.sqrt(np.vdot(r1, y).real)
+    if beta1 == 0.0:
+        return x.reshape(shape), dict(iters=0, history=[], converged=True)
+    oldb, beta, dbar, epsln, phibar = 0.0, beta1, 0.0, 0.0, beta1
+    cs, sn = -1.0, 0.0
+    w = np.zeros_like(c)
+    w2 = np.zeros_like(c)
+    r2 = r1.copy()
+    history = []
+    it = 0
+    while it < max_iter:
+        v = y / beta
+        y = H(v)
+        it += 1
+        if it >= 2:
+            y = y - (beta / oldb) * r1
+        alfa = np.vdot(v, y).real
+        y = y - (alfa / beta) * r2
+        r1, r2 = r2, y
+        y = Mi(r2)
+        oldb, beta = beta, np.sqrt(max(np.vdot(r2, y).real, 0.0))
+        oldeps = epsln
+        delta = cs * dbar + sn * alfa
+        gbar = sn * dbar - cs * alfa
+        epsln = sn * beta
+        dbar = -cs * beta
+        gamma = max(np.hypot(gbar, beta), np.finfo(float).tiny)
+        cs, sn = gbar / gamma, beta / gamma
+        phi = cs * phibar
+        phibar = sn * phibar
+        w1, w2 = w2, w
+        w = (v - oldeps * w1 - delta * w2) / gamma
+        x = x + phi * w
+        history.append(abs(phibar) / beta1)
+        if history[-1] <= tol or beta == 0.0:
+            break
+    return x.reshape(shape), dict(iters=it, history=history, converged=bool(history and history[-1] <= tol))

@@ -48,7 +48,8 @@ def _pc(args):
 
 def run(name, args):
     torch.cuda.init()
-    {"matvec": matvec, "sweep": sweep, "gyroid": gyroid, "adjoint": adjoint, "optimise": optimise}[name](args)
+    {"matvec": matvec, "sweep": sweep, "gyroid": gyroid, "adjoint": adjoint, "optimise": optimise,
+     "nearpole": nearpole}[name](args)
 
 
 def _events():
@@ -180,6 +181,49 @@ def gyroid(args):
                          refine_steps=infos[0]["refine_steps"], rel_residual=infos[0]["rel_residual"],
                          status=infos[0]["status"])
         plan.close()
+    print(json.dumps(res), flush=True)
+
+
+NEARPOLE_DELTAS = (-1e-2, -1e-3, -1e-4, -1e-5, -1e-6, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2)
+
+
+def woodpile_pole(n_harm, k0=2 * math.pi):
+    """The x-polarised mode pole eta of the woodpile along z at truncation
+    n_harm: FP64 sweep over [1.5, 1.9] k0 and the Eqs. 7-10 fit."""
+    plan = gsm.plan_for(wl.woodpile(), n_harm, precision=gsm.FP64, tol=1e-12)
+    _, diag = plan.retrieve_tensor(k0, [(1.5 * k0, 1.9 * k0)] * 3, 16)
+    plan.close()
+    return float(diag["eta"][0].real)
+
+
+def nearpole_solves(n_harm, eta, krylov, precision, tol, deltas=NEARPOLE_DELTAS, k0=2 * math.pi, max_iter=2000):
+    """Solves of the woodpile at kappa = eta (1 + delta), x polarisation along z:
+    the points around a mode pole where the paper finds that GMRES converges
+    and other iterative methods fail ("Calculation details")."""
+    pts = [wl.point(eta * (1 + d), (0, 0, 1), (1, 0, 0), k0) for d in deltas]
+    plan = gsm.plan_for(wl.woodpile(), n_harm, precision=precision, tol=tol, max_batch=len(pts), max_iter=max_iter,
+                        krylov=krylov)
+    E, infos, s = plan.solve(pts)
+    plan.close()
+    return pts, E, infos
+
+
+def nearpole(args):
+    """GMRES against BiCGSTAB around the woodpile's x-polarised pole (15^3
+    harmonics, 32^3 grid): products, refinement steps and status per point,
+    complex64 + refinement (tol 1e-8) and FP64 (tol 1e-10)."""
+    n_harm = (15, 15, 15)
+    eta = woodpile_pole(n_harm)
+    res = {"workload": "woodpile 15^3 harmonics, kappa = eta (1 + delta) around the x-polarised pole",
+           "eta_over_k0": eta / (2 * math.pi), "deltas": list(NEARPOLE_DELTAS)}
+    for kname, kr in (("gmres", gsm.GMRES), ("bicgstab", gsm.BICGSTAB)):
+        for pname, prec, tol in (("c64_refine", gsm.FP32_REFINE, 1e-8), ("fp64", gsm.FP64, 1e-10)):
+            t0 = time.perf_counter()
+            _, _, infos = nearpole_solves(n_harm, eta, kr, prec, tol)
+            res["%s_%s" % (kname, pname)] = {
+                "seconds": time.perf_counter() - t0,
+                "products": [i["iters"] for i in infos], "refine_steps": [i["refine_steps"] for i in infos],
+                "status": [i["status"] for i in infos], "rel_residual": [i["rel_residual"] for i in infos]}
     print(json.dumps(res), flush=True)
 
 

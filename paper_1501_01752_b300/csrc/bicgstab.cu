@@ -21,6 +21,7 @@
 // <r^, v> = 0, rho = 0 or omega = 0).  Inactive instances skip every kernel,
 // so all blocks of an instance take part in a reduction or none do.
 #include "kernels.h"
+#include "reduce.cuh"
 #include "vec.cuh"
 
 namespace gsm {
@@ -279,15 +280,21 @@ __global__ void __launch_bounds__(BT) k_bicg_update(BicgPtrs bp, typename Cx<R>:
 template <typename R>
 __global__ void __launch_bounds__(BT) k_bicg_sol(double2 *__restrict__ x64, long long xinst,
                                                  const typename Cx<R>::T *__restrict__ V, long long vinst, long long U,
-                                                 long long Us, const int *__restrict__ need) {
+                                                 long long Us, const int *__restrict__ need, double *partial,
+                                                 unsigned *counter, double *dnorm2) {
+  __shared__ double red[32];
   const int b = blockIdx.y;
   if (!need[b]) return;
   const typename Cx<R>::T *d = V + b * vinst + BS_D * Us;
   double2 *xb = x64 + b * xinst;
+  double acc = 0;   // ||d||^2: bounds the rounding error of a later r -= A d
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < U; e += (long long)gridDim.x * blockDim.x) {
     const double2 x = xb[e];
-    xb[e] = make_double2(x.x + (double)d[e].x, x.y + (double)d[e].y);
+    const double dx = (double)d[e].x, dy = (double)d[e].y;
+    xb[e] = make_double2(x.x + dx, x.y + dy);
+    acc += dx * dx + dy * dy;
   }
+  last_block_sum(acc, red, partial, counter, dnorm2, b, gridDim.x, blockIdx.x);
 }
 
 // WHILE condition of the captured iteration loop: any instance still active
@@ -322,7 +329,7 @@ template <typename R>
 cudaError_t launch_bicg_sol(double2 *x64, long long xinst, const typename Cx<R>::T *V, long long vinst,
                             const BicgPtrs &bp, const int *need, cudaStream_t st) {
   dim3 grid(bp.nblk, bp.B);
-  k_bicg_sol<R><<<grid, BT, 0, st>>>(x64, xinst, V, vinst, bp.U, bp.Us, need);
+  k_bicg_sol<R><<<grid, BT, 0, st>>>(x64, xinst, V, vinst, bp.U, bp.Us, need, bp.dpartial, bp.dcounter, bp.dnorm2);
   return cudaGetLastError();
 }
 

@@ -96,7 +96,7 @@ template <typename R> struct MatvecArgs {
   const int *jdev = nullptr;   // graph mode: X and Y advance by (*jdev) * jstride
   long long jstride = 0;
   int nact = 0;                // profiling only: instances still active (0 = all B), for the byte count
-  int yzv = 0;                 // complex64 pass 2: 1 = lane-shuffle transposes (k_yz_t8x2r),
+  int yzv = 1;                 // complex64 pass 2: 1 = lane-shuffle transposes (k_yz_t8x2r),
                                // 0 = team-buffer transposes (k_yz_t8x2)
 };
 
@@ -151,8 +151,14 @@ struct KrylovPtrs {
   double2 *y;               // [B][m]
   double *thresh;           // [B]
   int *kcount;              // [B]
-  float *scale32;           // [B]
+  float *scale32;           // [B] 1 / ||v_j|| of the vector the next product takes
   double *scale64;          // [B]
+  double *dnorm2;           // [B] ||d||^2 of the correction added to x by the last solution update
+  double *dpartial;         // [B][nblk] its block partials (shared with the product's norm partials)
+  unsigned *dcounter;       // [B] its last-block counters
+  double *svec;             // [B][m+1] 1 / ||v_i|| of every stored basis vector: GMRES keeps the
+                            // basis unnormalised (v_i = svec_i * V_i), the scales enter the dots,
+                            // the update coefficients and the solution update
   double *resid;            // [B]
   int force_reorth;         // 0: DGKS test, 1: always reorthogonalise, 2: never
   int nact;                 // profiling only: instances active in the step launched (0 = all B);
@@ -206,6 +212,9 @@ struct BicgPtrs {
   int *act;                 // [B] instance still iterating
   int *it;                  // [B] iterations of this cycle
   int max_it;               // iteration cap of a cycle
+  double *dnorm2;           // [B] ||d||^2 of the correction added to x (k_bicg_sol)
+  double *dpartial;         // [B][nblk] its block partials
+  unsigned *dcounter;       // [B] its last-block counters
 };
 template <typename R>
 cudaError_t launch_bicg_step(int which, const BicgPtrs &bp, typename Cx<R>::T *V, long long vinst, cudaStream_t st);

@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
                                              int nv, int wi, const int *__restrict__ act,
                                              const int *__restrict__ gate, double *partial, unsigned *counter,
                                              double *out, int ostride, int nblk, const int *__restrict__ jdev,
-                                             const int *__restrict__ alist, int bcap) {
+                                             const int *__restrict__ alist, int bcap,
+                                             const double *__restrict__ svec, int sstride) {
   using C = typename Cx<R>::T;
   constexpr int EPT = EptDots<R>::v, NW = KT / 32, CH = 4, NA = 2 * GV + 1;
   __shared__ double wsum[NA][NW];
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
       const double *pk = pin + (long long)k * nblk;
       double s = 0;
       for (int q = 0; q < nblk; ++q) s += __ldcg(pk + q);
+      if (svec && k < 2 * nv) s *= svec[(long long)b * sstride + (k >> 1)];   // <v_i, w> = s_i <V_i, w>
       out[(long long)b * ostride + k] = s;
     }
   } else {
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
       double s = 0;
       for (int q = lane; q < nblk; q += 32) s += __ldcg(pk + q);
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (svec && k < 2 * nv) s *= svec[(long long)b * sstride + (k >> 1)];
       if (lane == 0) out[(long long)b * ostride + k] = s;
     }
   }
@@ -156,7 +159,8 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
                                                const int *__restrict__ act, const int *__restrict__ gate,
                                                double *partial, unsigned *counter, double *wn_out,
                                                int *gate_out, int force, const int *__restrict__ jdev,
-                                               const int *__restrict__ alist, int nblk, int bcap) {
+                                               const int *__restrict__ alist, int nblk, int bcap,
+                                               const double *__restrict__ svec, int sstride) {
   using C = typename Cx<R>::T;
   constexpr int EPT = Ept<R>::v;
   if (jdev) {
@@ -174,8 +178,11 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
   const int b = alist[1 + a];
   (void)act;
   if (gate && !gate[b]) return;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x)
-    hs[i] = mk((R)h[(long long)b * hstride + 2 * i], (R)h[(long long)b * hstride + 2 * i + 1]);
+  // the coefficient of the stored (unnormalised) V_i is h_i s_i
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const double si = svec ? svec[(long long)b * sstride + i] : 1.0;
+    hs[i] = mk((R)(h[(long long)b * hstride + 2 * i] * si), (R)(h[(long long)b * hstride + 2 * i + 1] * si));
+  }
   __syncthreads();
   C *Vb = V + b * vinst;
   C *W = Vb + (long long)wi * Us;
@@ -278,6 +285,7 @@ __global__ void __launch_bounds__(32 * FIN_W) k_finish(KrylovPtrs k, int j) {
     k.kcount[b] = j + 1;
     k.scale32[b] = hn > 0 ? (float)(1.0 / hn) : 0.f;
     k.scale64[b] = hn > 0 ? 1.0 / hn : 0.0;
+    k.svec[(long long)b * (m + 1) + j + 1] = hn > 0 ? 1.0 / hn : 0.0;
     const double r = hypot(g[j + 1].x, g[j + 1].y);
     k.resid[b] = r;
     if (r <= k.thresh[b] || hn == 0.0 || j + 1 >= m) k.act[b] = 0;
@@ -331,25 +339,34 @@ __global__ void __launch_bounds__(KT) k_sol_update(double2 *__restrict__ x64, lo
                                                    typename Cx<R>::T *__restrict__ V, long long vinst,
                                                    long long U, long long Us, const double2 *__restrict__ y, int m,
                                                    const int *__restrict__ kcount, const int *__restrict__ need,
-                                                   int dslot) {
+                                                   int dslot, const double *__restrict__ svec, double *partial,
+                                                   unsigned *counter, double *dnorm2) {
   using C = typename Cx<R>::T;
   __shared__ C ys[MAXM];
+  __shared__ double red[32];
   const int b = blockIdx.y;
   if (!need[b]) return;
   const int n = kcount[b];
   if (n == 0) return;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = mk((R)y[(long long)b * m + i].x, (R)y[(long long)b * m + i].y);
+  // V y over the normalised basis = sum_i (y_i s_i) V_i over the stored one
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double si = svec[(long long)b * (m + 1) + i];
+    ys[i] = mk((R)(y[(long long)b * m + i].x * si), (R)(y[(long long)b * m + i].y * si));
+  }
   __syncthreads();
   C *Vb = V + b * vinst;
   double2 *xb = x64 + b * xinst;
   C *dv = dslot >= 0 ? Vb + (long long)dslot * Us : nullptr;   // keeps the correction d for r -= A d
+  double acc = 0;   // ||d||^2: bounds the rounding error of a later r -= A d
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < U; e += (long long)gridDim.x * blockDim.x) {
     C d = mk((R)0, (R)0);
     for (int i = 0; i < n; ++i) d = cadd(d, cmul(ys[i], Vb[(long long)i * Us + e]));
     double2 xv = xb[e];
     xb[e] = mk(xv.x + (double)d.x, xv.y + (double)d.y);
     if (dv) dv[e] = d;
+    acc += (double)d.x * d.x + (double)d.y * d.y;
   }
+  last_block_sum(acc, red, partial, counter, dnorm2, b, gridDim.x, blockIdx.x);
 }
 
 // Right-preconditioned Krylov cycles solve A M^{-1} u = r, so the
@@ -364,15 +381,19 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
                                                       typename Cx<R>::T *__restrict__ V, long long vinst, long long Us,
                                                       const double2 *__restrict__ y, int m,
                                                       const int *__restrict__ kcount, const int *__restrict__ need,
-                                                      int dslot, int src) {
+                                                      int dslot, int src, const double *__restrict__ svec,
+                                                      double *partial, unsigned *counter, double *dnorm2) {
   using C = typename Cx<R>::T;
   __shared__ C ys[MAXM];
+  __shared__ double red[32];
   const int b = blockIdx.y;
   if (!need[b]) return;
   const int n = src >= 0 ? 1 : kcount[b];
   if (n == 0) return;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    ys[i] = src >= 0 ? mk((R)1, (R)0) : mk((R)y[(long long)b * m + i].x, (R)y[(long long)b * m + i].y);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double si = src >= 0 ? 1.0 : svec[(long long)b * (m + 1) + i];   // GMRES: unnormalised basis
+    ys[i] = src >= 0 ? mk((R)1, (R)0) : mk((R)(y[(long long)b * m + i].x * si), (R)(y[(long long)b * m + i].y * si));
+  }
   __syncthreads();
   C *Vb = V + b * vinst;
   double2 *xb = x64 + b * xinst;
@@ -380,6 +401,7 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
   const C *V0 = Vb + (src >= 0 ? (long long)src * Us : 0);
   const long long Nh = g.Nh;
   const R pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
+  double acc = 0;   // ||M^{-1} u||^2, the correction added to x
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < Nh; e += (long long)gridDim.x * blockDim.x) {
     C d[3];
 #pragma unroll
@@ -417,9 +439,12 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double2 xv = xb[c * Nh + e];
-      xb[c * Nh + e] = mk(xv.x + (double)(al * d[c].x + f * kc[c] * kr), xv.y + (double)(al * d[c].y + f * kc[c] * ki));
+      const double cx = (double)(al * d[c].x + f * kc[c] * kr), cy = (double)(al * d[c].y + f * kc[c] * ki);
+      xb[c * Nh + e] = mk(xv.x + cx, xv.y + cy);
+      acc += cx * cx + cy * cy;
     }
   }
+  last_block_sum(acc, red, partial, counter, dnorm2, b, gridDim.x, blockIdx.x);
 }
 
 // r -= A d with A d from the complex64 product, and ||r||^2 (last block).
@@ -564,20 +589,20 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
   const double vb = (double)sizeof(typename Cx<R>::T) * k.U * (k.nact > 0 ? k.nact : k.B);
   if (prof) prof->begin(KIND_DOTS, st);
   k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs, k.nblk, k.jdev,
-                                    k.alist, k.bcap);
+                                    k.alist, k.bcap, k.svec, k.m + 1);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot0, hs, k.act, nullptr, k.partial, k.counter, k.wn0,
-                                   k.gate, k.force_reorth, k.jdev, k.alist, k.nblk, k.bcap);
+                                   k.gate, k.force_reorth, k.jdev, k.alist, k.nblk, k.bcap, k.svec, k.m + 1);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   if (k.force_reorth == 2) return cudaGetLastError();   // no second pass: gate was cleared
   if (prof) prof->begin(KIND_DOTS, st);
   k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs, k.nblk, k.jdev,
-                                    k.alist, k.bcap);
+                                    k.alist, k.bcap, k.svec, k.m + 1);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot1, hs, k.act, k.gate, k.partial, k.counter, k.wn1,
-                                   nullptr, 0, k.jdev, k.alist, k.nblk, k.bcap);
+                                   nullptr, 0, k.jdev, k.alist, k.nblk, k.bcap, k.svec, k.m + 1);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   return cudaGetLastError();
 }
@@ -619,7 +644,8 @@ cudaError_t launch_sol_update(const KrylovPtrs &k, double2 *x64, long long xinst
                               long long vinst, const int *need, int dslot, cudaStream_t st, Profiler *prof) {
   dim3 grid(k.nblk, k.B);
   if (prof) prof->begin(KIND_OTHER, st);
-  k_sol_update<R><<<grid, KT, 0, st>>>(x64, xinst, V, vinst, k.U, k.Us, k.y, k.m, k.kcount, need, dslot);
+  k_sol_update<R><<<grid, KT, 0, st>>>(x64, xinst, V, vinst, k.U, k.Us, k.y, k.m, k.kcount, need, dslot, k.svec,
+                                       k.dpartial, k.dcounter, k.dnorm2);
   if (prof) prof->end(KIND_OTHER, st, 0.0);
   return cudaGetLastError();
 }
@@ -631,7 +657,7 @@ cudaError_t launch_sol_update_pc(const KrylovPtrs &k, const Geo &g, const Inst *
   dim3 grid(k.nblk, k.B);
   if (prof) prof->begin(KIND_OTHER, st);
   k_sol_update_pc<R><<<grid, KT, 0, st>>>(g, inst, iden, x64, xinst, V, vinst, k.Us, k.y, k.m, k.kcount, need, dslot,
-                                          src);
+                                          src, k.svec, k.dpartial, k.dcounter, k.dnorm2);
   if (prof) prof->end(KIND_OTHER, st, 0.0);
   return cudaGetLastError();
 }

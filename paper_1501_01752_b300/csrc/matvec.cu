@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
                         long long xstride, typename Cx<R>::T *__restrict__ Y, long long ystride,
                         const int *__restrict__ act, const Inst *__restrict__ inst, const R *__restrict__ iden,
                         const typename Cx<R>::T *__restrict__ twg, int rows, int nchunk, double *partial,
-                        unsigned *counter, double *norm_out, const int *__restrict__ jdev, long long jstride) {
+                        unsigned *counter, double *norm_out, const int *__restrict__ jdev, long long jstride,
+                        const R *__restrict__ scale) {
   using C = typename Cx<R>::T;
   if (jdev) {
     X += (long long)(*jdev) * jstride;
@@ -225,7 +226,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
       u1 = mk(id * (kb2 * u1.x - ky * ku.x), id * (kb2 * u1.y - ky * ku.y));
       u2 = mk(id * (kb2 * u2.x - kz * ku.x), id * (kb2 * u2.y - kz * ku.y));
     }
-    C y0 = csub(Xb[h], u0), y1 = csub(Xb[Nh + h], u1), y2 = csub(Xb[2 * Nh + h], u2);
+    // the identity term takes the input as pass 1 did (scaled by 1 / ||v_j||:
+    // the stored Krylov vector is unnormalised)
+    const R sx = scale ? scale[b] : (R)1;
+    C y0 = csub(cscale(Xb[h], sx), u0), y1 = csub(cscale(Xb[Nh + h], sx), u1), y2 = csub(cscale(Xb[2 * Nh + h], sx), u2);
     if (MODE & 1) {
       C b0 = czero<C>(), b1 = czero<C>(), b2 = czero<C>();
       if (h == h0) {
@@ -347,7 +351,7 @@ cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *pro
   cudaFuncSetAttribute(k_inv_x<R, M, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
   k_inv_x<R, M, HF><<<grid, threads, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst, a.iden, \
                                                  a.tw, rows, nchunk, a.partial, a.counter, a.norm_out, a.jdev,  \
-                                                 a.jstride)
+                                                 a.jstride, a.scale)
     if (a.mode == 0) { if (a.form) { GSM_P3(0, 1); } else { GSM_P3(0, 0); } }
     else if (a.mode == 1) { if (a.form) { GSM_P3(1, 1); } else { GSM_P3(1, 0); } }
     else if (a.mode == 2) { GSM_P3(2, 0); }

@@ -579,7 +579,8 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
                                                  const int *__restrict__ act, const Inst *__restrict__ inst,
                                                  const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,
                                                  int rows, double *partial, unsigned *counter, double *norm_out,
-                                                 const int *__restrict__ jdev, long long jstride, int pc, int nog) {
+                                                 const int *__restrict__ jdev, long long jstride, int pc, int nog,
+                                                 const R *__restrict__ scale) {
   using C = typename Cx<R>::T;
   using IO = typename Io<R>::T;
   using F = Team8<L0>;
@@ -669,7 +670,16 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   const int h0 = (g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
   IO *Yb = Y + b * ystride;
   R acc = 0;   // this thread's share of ||y||^2 (a few harmonics), widened once
+  // the identity term takes the input as pass 1 did: scaled by 1 / ||v_j||
+  // (the stored Krylov vector is unnormalised)
+  const bool sc = scale != nullptr;
+  const R sx = sc ? scale[b] : (R)1;
   auto body = [&](int row, int mx, C y0, C y1, C y2, R id) {
+    if (sc) {
+      y0 = cscale(y0, sx);
+      y1 = cscale(y1, sx);
+      y2 = cscale(y2, sx);
+    }
     const int h = (r0 + row) * N0 + mx;
     const C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
             u2 = S3[(2 * rows + row) * P + mx];
@@ -845,7 +855,7 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   cudaFuncSetAttribute(k_inv_x_t8<R, 128, M, TX, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
   k_inv_x_t8<R, 128, M, TX, HF><<<grid, TX, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,   \
                                                         a.iden, a.tw, rows, a.partial, a.counter, a.norm_out,     \
-                                                        a.jdev, a.jstride, a.pc, a.mode >= 2)
+                                                        a.jdev, a.jstride, a.pc, a.mode >= 2, a.scale)
     if (a.form) { if (a.mode & 1) { GSM_P3X(1, 1); } else { GSM_P3X(0, 1); } }
     else { if (a.mode & 1) { GSM_P3X(1, 0); } else { GSM_P3X(0, 0); } }
 #undef GSM_P3X
@@ -858,7 +868,7 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   cudaFuncSetAttribute(k_inv_x_t8<R, L0, M, TT, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
   k_inv_x_t8<R, L0, M, TT, HF><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,     \
                                                        a.iden, a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, \
-                                                       a.jstride, a.pc, a.mode >= 2)
+                                                       a.jstride, a.pc, a.mode >= 2, a.scale)
   if (g.L[0] == 64) {
     if (a.form) { if (a.mode & 1) { GSM_P3(64, 1, 1); } else { GSM_P3(64, 0, 1); } }
     else { if (a.mode & 1) { GSM_P3(64, 1, 0); } else { GSM_P3(64, 0, 0); } }
