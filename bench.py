@@ -454,6 +454,13 @@ def main():
         line["oracle_parity"] = {"points": len(errs), "field_rel_err_max": max(errs) if errs else None,
                                  "note": "GPU FP32+refine vs oracle FP64 GMRES, both to residual 1e-8"}
     plan.close()
+    # the C3 resonance sweep of the retrieval (512 points of truncations
+    # 15/21/31 through gsm_sweep, batches across truncations), end to end
+    # with the pole fits: a secondary figure, not the headline
+    from paper_1501_01752_b300 import bench_workloads
+    sw = bench_workloads.sweep_c3(args)
+    line["sweep_c3"] = {k: sw[k] for k in ("workload", "solves_per_s", "seconds", "retrieval_host_ms", "iters_mean",
+                                           "rel_residual_max", "max_batch", "batches")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -71,10 +71,12 @@ struct Work {
   double *mv_partial = nullptr, *mv_norm = nullptr;
   unsigned *mv_counter = nullptr;
   int *jcount = nullptr;    // device Arnoldi step counter of the captured cycle
+  int mvb = 0;              // blocks per instance the norm partials of the products have room for
   KrylovPtrs k{};
   // a captured cycle holds its kernels' arguments by value, among them the
-  // level's multiplier (D, Dp): it is reused only while those are unchanged
-  struct Cycle { int B, m, adj, force, prec, pc; const void *D, *Dp; cudaGraph_t graph; cudaGraphExec_t exec; };
+  // levels' multipliers (D, Dp) and the batch's split into truncations: it is
+  // reused only while those are unchanged (sig)
+  struct Cycle { int B, m, adj, force, prec; std::string sig; cudaGraph_t graph; cudaGraphExec_t exec; };
   std::vector<Cycle> cycles;
   void drop_graphs() {
     for (auto &c : cycles) {
@@ -114,6 +116,8 @@ struct gsm_plan_s {
   bool team_only = false;  // GSM_FFT_PATH=team: shared-memory FFTs everywhere
   bool use_graphs = true;  // inner GMRES cycles as one graph launch (GSM_GRAPHS=0 disables)
   bool no_packed = false;  // GSM_PACKED=0: complex64 pass 2 one x plane per block instead of packed plane pairs
+  double2 *e0_dev = nullptr;   // gsm_sweep: E_0 of the instances of a batch
+  int e0_cap = 0;
   int yzv = 1;             // complex64 pass 2 with lane-shuffle transposes (k_yz_t8x2r); GSM_YZ=smem:
                            // the team-buffer transposes of k_yz_t8x2
   cudaStream_t cap_st = nullptr;  // private stream used only to capture graphs
@@ -194,6 +198,8 @@ static Geo make_geo(const gsm_plan_desc &d, const int N[3], const int Lplan[3]) 
   g.Nh = (long long)N[0] * N[1] * N[2];
   g.U = 3 * g.Nh;
   g.Tsz = 3LL * g.L[0] * N[1] * N[2];
+  g.Tst = g.Tsz;
+  g.ist = g.Nh;
   return g;
 }
 
@@ -237,6 +243,13 @@ static int krylov_blocks(const Geo &g, int B) {
   return (int)std::min(per, cap);
 }
 
+// Most blocks per instance of any product pass 3 or vector kernel on this
+// geometry: the room per instance of the norm partials
+static int mv_blocks(const Geo &g) {
+  return std::max(std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8)),
+                  std::max(matvec_reg_blocks_pass3(g), krylov_blocks(g, 1)));
+}
+
 // Carve the workspace of B instances out of `base` (nullptr: only measure).
 // The same routine sizes and assigns, so every array lies inside the block.
 static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nblk, char *base) {
@@ -258,8 +271,8 @@ static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nbl
   w.idendf = (dfl *)take((size_t)B * g.Nh * 8);
   w.inst = (Inst *)take((size_t)B * sizeof(Inst));
   w.need = (int *)take((size_t)B * 4);
-  const int mvb = std::max(std::max(matvec_blocks_pass3(g, 16), matvec_blocks_pass3(g, 8)),
-                           std::max(matvec_reg_blocks_pass3(g), krylov_blocks(g, 1)));
+  const int mvb = mv_blocks(g);
+  w.mvb = mvb;
   w.mv_partial = (double *)take((size_t)B * mvb * 8);
   w.mv_norm = (double *)take((size_t)B * 8);
   w.mv_counter = (unsigned *)take((size_t)B * 4);
@@ -289,6 +302,7 @@ static size_t work_layout(Work &w, const Geo &g, int B, int m, int prec, int nbl
   k.scale32 = (float *)take((size_t)B * 4);
   k.scale64 = (double *)take((size_t)B * 8);
   k.svec = (double *)take((size_t)B * (m + 1) * 8);
+  k.ulen = (long long *)take((size_t)B * 8);
   k.dnorm2 = (double *)take((size_t)B * 8);
   k.dpartial = w.mv_partial;   // the solution update runs between the products that use them
   k.dcounter = w.mv_counter;
@@ -506,6 +520,7 @@ static gsm_status get_level(gsm_plan_t *p, const int N[3], Level **out) {
       }
     if (mixed) {
       alt.g.Tsz = 3LL * alt.g.L[0] * alt.g.N[1] * alt.g.N[2];
+      alt.g.Tst = alt.g.Tsz;
       if ((s = build_multiplier(p, lv)) || (s = build_multiplier(p, alt))) {
         alt.free_multipliers();
         return s;
@@ -719,13 +734,28 @@ static cudaError_t autotune(gsm_plan_t *p, Level &lv, const MatvecArgs<R> &base)
 // moves the device step counter and sets the loop condition.  Built once per
 // workspace, batch size, basis length and operator direction; nullptr if the
 // runtime refuses (the caller then launches step by step).
+// One truncation's share of a batch: instances b0 .. b0 + n - 1 (contiguous,
+// sorted by truncation), solved with the level's multiplier and geometry and
+// the batch's per-instance strides.
+struct Part {
+  Level *lv;
+  int b0, n;
+};
+
 template <typename R>
-static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, const MatvecArgs<R> &mv,
-                                   const KrylovPtrs &k, typename Cx<R>::T *V, long long vinst, long long Us, int adj) {
+static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const std::vector<Part> &parts,
+                                   const std::vector<MatvecArgs<R>> &mvs, const KrylovPtrs &k,
+                                   typename Cx<R>::T *V, long long vinst, long long Us, int adj) {
   const int prec = sizeof(R) == 4;
+  std::string sig;
+  for (size_t i = 0; i < parts.size(); ++i) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "%p:%d:%d:%p:%p:%d;", (void *)parts[i].lv, parts[i].b0, parts[i].n,
+                  (const void *)mvs[i].D, (const void *)mvs[i].Dp, mvs[i].pc);
+    sig += buf;
+  }
   for (auto &c : w->cycles)
-    if (c.B == k.B && c.m == k.m && c.adj == adj && c.force == k.force_reorth && c.prec == prec && c.D == mv.D &&
-        c.Dp == mv.Dp && c.pc == mv.pc)
+    if (c.B == k.B && c.m == k.m && c.adj == adj && c.force == k.force_reorth && c.prec == prec && c.sig == sig)
       return c.exec;
   if (!p->cap_st && cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -733,11 +763,6 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
   }
   KrylovPtrs kg = k;
   kg.jdev = w->jcount;
-  MatvecArgs<R> mg = mv;
-  mg.X = V;
-  mg.Y = V + Us;
-  mg.jdev = w->jcount;
-  mg.jstride = Us;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
@@ -757,10 +782,19 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
     ok = cudaStreamBeginCaptureToGraph(p->cap_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
          cudaSuccess;
     if (ok) {
-      bool launched = matvec<R>(p, lv, mg, nullptr, p->cap_st) == cudaSuccess &&
-                      launch_arnoldi_ortho<R>(kg, V, vinst, 0, p->cap_st, nullptr) == cudaSuccess &&
-                      launch_finish(kg, 0, p->cap_st) == cudaSuccess &&
-                      launch_advance(kg, h, p->cap_st) == cudaSuccess;
+      // every truncation's product of its instances' current vector, then
+      // one Gram-Schmidt step over the whole batch
+      bool launched = true;
+      for (size_t i = 0; i < parts.size() && launched; ++i) {
+        MatvecArgs<R> mg = mvs[i];
+        mg.X = V + parts[i].b0 * vinst;
+        mg.Y = mg.X + Us;
+        mg.jdev = w->jcount;
+        mg.jstride = Us;
+        launched = matvec<R>(p, *parts[i].lv, mg, nullptr, p->cap_st) == cudaSuccess;
+      }
+      launched = launched && launch_arnoldi_ortho<R>(kg, V, vinst, 0, p->cap_st, nullptr) == cudaSuccess &&
+                 launch_finish(kg, 0, p->cap_st) == cudaSuccess && launch_advance(kg, h, p->cap_st) == cudaSuccess;
       cudaGraph_t out = nullptr;
       ok = cudaStreamEndCapture(p->cap_st, &out) == cudaSuccess && launched;
     }
@@ -774,8 +808,23 @@ static cudaGraphExec_t cycle_graph(gsm_plan_t *p, Work *w, const Level &lv, cons
     if (graph) cudaGraphDestroy(graph);
     return nullptr;
   }
-  w->cycles.push_back({k.B, k.m, adj, k.force_reorth, prec, mv.pc, mv.D, mv.Dp, graph, exec});
+  w->cycles.push_back({k.B, k.m, adj, k.force_reorth, prec, sig, graph, exec});
   return exec;
+}
+
+// The Krylov arrays of instances b0 .. b0 + n - 1 as a batch of its own (for
+// the per-truncation kernels: solution updates)
+static KrylovPtrs part_ptrs(const KrylovPtrs &k, int b0, int n, long long U) {
+  KrylovPtrs q = k;
+  q.B = n;
+  q.U = U;
+  q.y += (long long)b0 * k.m;
+  q.kcount += b0;
+  q.svec += (long long)b0 * (k.m + 1);
+  q.dnorm2 += b0;
+  q.dpartial += (long long)b0 * k.nblk;
+  q.dcounter += b0;
+  return q;
 }
 
 // One BiCGSTAB iteration (two products and five vector kernels) for the
@@ -828,9 +877,11 @@ static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const Mat
   const int prec = sizeof(R) == 4;
   if (p->use_graphs && !prof) {
     cudaGraphExec_t exec = nullptr;
+    char sigb[96];
+    std::snprintf(sigb, sizeof sigb, "bicg:%p:%p:%d", (const void *)mv.D, (const void *)mv.Dp, mv.pc);
+    const std::string sig = sigb;
     for (auto &c : w->cycles)
-      if (c.B == bp.B && c.m == BS_COUNT - 1 && c.adj == (int)adj && c.force == -1 && c.prec == prec &&
-          c.D == mv.D && c.Dp == mv.Dp && c.pc == mv.pc)
+      if (c.B == bp.B && c.m == BS_COUNT - 1 && c.adj == (int)adj && c.force == -1 && c.prec == prec && c.sig == sig)
         exec = c.exec;
     if (!exec) {
       if (!p->cap_st && cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -866,7 +917,7 @@ static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const Mat
           if (graph) cudaGraphDestroy(graph);
           exec = nullptr;
         } else {
-          w->cycles.push_back({bp.B, BS_COUNT - 1, (int)adj, -1, prec, mv.pc, mv.D, mv.Dp, graph, exec});
+          w->cycles.push_back({bp.B, BS_COUNT - 1, (int)adj, -1, prec, sig, graph, exec});
         }
       }
     }
@@ -895,12 +946,36 @@ static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const Mat
 // one level.  b = a at m = 0, with a the point's polarisation or, when rhs is
 // given, rhs[6 b .. 6 b + 5].
 template <typename R>
-static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *pts, gsm_info *infos,
-                              double2 **out_x, bool adj, const double *rhs) {
+static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int B, const gsm_point *pts,
+                              gsm_info *infos, double2 **out_x, long long *out_stride, bool adj, const double *rhs) {
   using C = typename Cx<R>::T;
-  const Geo &g = lv.g;
   const int prec = sizeof(R) == 4 ? 1 : 0;
   const bool bicg = p->d.krylov == GSM_BICGSTAB;
+  const int NP = (int)parts.size();
+  const bool multi = NP > 1;
+  if (multi && bicg) return fail(p, GSM_ERR_STATE, "internal: BiCGSTAB batches hold one truncation");
+  Level &lv = *parts[0].lv;
+  // the batch's geometry: the level's own, or for several truncations the
+  // elementwise-largest box, whose sizes give every instance the same strides
+  Geo g = lv.g;
+  if (multi) {
+    int Nm[3] = {0, 0, 0};
+    for (const Part &q : parts)
+      for (int a = 0; a < 3; ++a) Nm[a] = std::max(Nm[a], q.lv->g.N[a]);
+    g = make_geo(p->d, Nm, p->L);
+    for (const Part &q : parts)
+      if (q.lv->g.U > g.U || q.lv->g.Tsz > g.Tsz || q.lv->g.Nh > g.Nh)
+        return fail(p, GSM_ERR_STATE, "internal: a truncation exceeds the batch's largest box");
+  }
+  // per-part geometries with the batch's strides of T and of the per-harmonic arrays
+  std::vector<Geo> gp(NP);
+  std::vector<int> part_of(B);
+  for (int i = 0; i < NP; ++i) {
+    gp[i] = parts[i].lv->g;
+    gp[i].Tst = g.Tsz;
+    gp[i].ist = g.Nh;
+    for (int b = parts[i].b0; b < parts[i].b0 + parts[i].n; ++b) part_of[b] = i;
+  }
   // GMRES keeps m + 1 basis vectors per instance, BiCGSTAB seven (slots BS_*)
   const int m = bicg ? BS_COUNT - 1 : capped_restart(p->d, g, B, prec);
   if (m < 2) return fail(p, GSM_ERR_NOMEM, "hbm_cap_bytes leaves fewer than 3 Krylov vectors");
@@ -909,11 +984,14 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   Work *w;
   gsm_status s = get_work(p, g, B, m, prec, &w);
   if (s) return s;
+  for (int i = 0; i < NP; ++i)
+    if (mv_blocks(gp[i]) > w->mvb) return fail(p, GSM_ERR_STATE, "internal: norm partials too small for a truncation");
   KrylovPtrs k = w->k;
   k.B = B;
   k.m = m;
   k.nblk = krylov_blocks(g, B);
   k.bcap = krylov_blocks(g, 1);
+  if (!multi) k.ulen = nullptr;   // every instance's vectors are Us long
   // complex64 inner solves stop at inner_tol >= 1e-6, far above the level
   // (~1e-7 relative) where classical Gram-Schmidt without reorthogonalisation
   // loses orthogonality, so they skip the second pass; FP64 solves keep the
@@ -941,7 +1019,7 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   // pinned staging: instance parameters and the small per-cycle arrays
   auto al = [](size_t n) { return (n + 63) & ~(size_t)63; };
   const size_t stage = al(B * sizeof(Inst)) + al(B * 4) + al(B * 8) + al(B * 4) + al(B * 8) + al(B * 16) +
-                       al(B * 8) + al(B * 4) + al(B * 8);
+                       al(B * 8) + al(B * 4) + al(B * 8) + al(B * 8);
   if ((s = ensure_pinned(p, stage))) return s;
   char *sp = p->pin;
   auto grab = [&](size_t n) { char *r = sp; sp += al(n); return (void *)r; };
@@ -954,23 +1032,32 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   double *h_rn = (double *)grab(B * 8);
   int *h_kc = (int *)grab(B * 4);
   double *h_dn = (double *)grab(B * 8);
+  long long *h_ul = (long long *)grab(B * 8);
   // right preconditioner (set_precond): Eq. 4 with the lane-team product,
   // forward solves only (GSM_PRECOND_NONE in the plan turns it off)
-  const bool pc = !adj && p->d.form == GSM_FORM_E && p->d.precond == GSM_PRECOND_AUTO && !p->team_only &&
-                  reg_path_ok(g) && std::fabs(lv.delta0) >= 1.0;
+  std::vector<char> pcp(NP);
+  for (int i = 0; i < NP; ++i)
+    pcp[i] = !adj && p->d.form == GSM_FORM_E && p->d.precond == GSM_PRECOND_AUTO && !p->team_only &&
+             reg_path_ok(gp[i]) && std::fabs(parts[i].lv->delta0) >= 1.0;
   for (int b = 0; b < B; ++b) {
-    if ((s = make_inst(p, pts[b], g, hI[b]))) return s;
+    const int i = part_of[b];
+    if ((s = make_inst(p, pts[b], gp[i], hI[b]))) return s;
     if (rhs)
-      for (int i = 0; i < 6; ++i) hI[b].a[i] = rhs[6 * b + i];
-    if (pc) set_precond(hI[b], g, lv.delta0);
+      for (int c = 0; c < 6; ++c) hI[b].a[c] = rhs[6 * b + c];
+    if (pcp[i]) set_precond(hI[b], gp[i], parts[i].lv->delta0);
+    h_ul[b] = padded(gp[i].U);
   }
   cudaStream_t st = p->st;
   Profiler *prof = p->prof.on ? &p->prof : nullptr;
   CK(cudaMemcpyAsync(w->inst, hI, B * sizeof(Inst), cudaMemcpyHostToDevice, st));
-  CK(launch_iden(g, w->inst, B, w->iden64, w->iden32, st, w->idendf));
+  if (multi) CK(cudaMemcpyAsync(k.ulen, h_ul, B * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(w->x64, 0, (size_t)B * g.U * 16, st));
-  CK(launch_set_rhs(w->r64, g.U, g, w->inst, B, st));
-  p->launches += 2;
+  for (int i = 0; i < NP; ++i) {
+    const int b0 = parts[i].b0, n = parts[i].n;
+    CK(launch_iden(gp[i], w->inst + b0, n, w->iden64 + b0 * g.Nh, w->iden32 + b0 * g.Nh, st, w->idendf + b0 * g.Nh));
+    CK(launch_set_rhs(w->r64 + b0 * g.U, g.U, gp[i], w->inst + b0, n, st));
+    p->launches += 2;
+  }
   const double tol = tol_of(p->d), itol = inner_tol_of(p->d);
   const int max_it = max_iter_of(p->d);
   std::vector<double> bnorm(B), rnorm(B);
@@ -988,73 +1075,82 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
   C *V = (C *)w->V;
   const long long Us = padded(g.U);
   const long long vinst = (long long)(m + 1) * Us;
-  CK(launch_zero_pads<C>(V, (long long)B * (m + 1), g.U, Us, st));
-  p->launches++;
-  MatvecArgs<R> mv;
-  mv.g = g;
-  mv.B = B;
-  mv.T = (C *)w->T;
-  mv.D = sizeof(R) == 4 ? (const R *)lv.D32 : (const R *)lv.D64;
-  mv.Dp = sizeof(R) == 4 ? lv.D32p : nullptr;
-  mv.act = k.act;
-  mv.inst = w->inst;
-  mv.iden = sizeof(R) == 4 ? (const R *)w->iden32 : (const R *)w->iden64;
-  mv.tw = sizeof(R) == 4 ? (const C *)p->tw32 : (const C *)p->tw64;
-  mv.xstride = vinst;
-  mv.ystride = vinst;
-  mv.write_back = 0;   // the basis stays unnormalised: pass 1 scales its input by 1 / ||v_j|| on the fly
-  mv.mode = adj ? 2 : 0;
-  mv.form = p->d.form;
-  mv.pc = pc ? 1 : 0;
-  mv.scale = sizeof(R) == 4 ? (const R *)k.scale32 : (const R *)k.scale64;
-  MatvecArgs<double> rs;  // FP64 residual b - A x
-  rs.g = g;
-  rs.B = B;
-  rs.X = w->x64;
-  rs.xstride = g.U;
-  rs.Y = w->r64;
-  rs.ystride = g.U;
-  rs.T = w->T;
-  rs.D = lv.D64;
-  rs.act = w->need;
-  rs.inst = w->inst;
-  rs.iden = w->iden64;
-  rs.tw = p->tw64;
-  rs.mode = adj ? 3 : 1;
-  rs.form = p->d.form;
-  rs.partial = w->mv_partial;
-  rs.counter = w->mv_counter;
-  rs.norm_out = w->mv_norm;
-  // the same residual in double-float arithmetic on the FP32 pipes (refined
-  // solves on lane-team levels unless the plan asks for FP64)
-  const bool df_resid = prec && !adj && p->d.residual == GSM_RESID_AUTO && !p->team_only && reg_path_ok(g) &&
-                        lv.Ddf != nullptr;
-  MatvecArgs<dfl> rd;
-  rd.g = g;
-  rd.B = B;
-  rd.X = w->x64;
-  rd.xstride = g.U;
-  rd.Y = w->r64;
-  rd.ystride = g.U;
-  rd.T = reinterpret_cast<dcx *>(w->T);
-  rd.D = lv.Ddf;
-  rd.act = w->need;
-  rd.inst = w->inst;
-  rd.iden = w->idendf;
-  rd.tw = p->twdf;
-  rd.mode = 1;
-  rd.form = p->d.form;
-  rd.partial = w->mv_partial;
-  rd.counter = w->mv_counter;
-  rd.norm_out = w->mv_norm;
-  // block sizes of the lane-team kernels: measured on this batch, first use only
-  {
-    MatvecArgs<R> tune = mv;
-    tune.X = V;
-    tune.Y = V + Us;
-    CK(cudaMemsetAsync(V, 0, (size_t)2 * Us * sizeof(C), st));
-    CK(autotune<R>(p, lv, tune));
+  for (int i = 0; i < NP; ++i) {
+    CK(launch_zero_pads<C>(V + parts[i].b0 * vinst, (long long)parts[i].n * (m + 1), gp[i].U, Us, st));
+    p->launches++;
   }
+  // the working-precision product of each part (Krylov vectors V, stride vinst)
+  std::vector<MatvecArgs<R>> mvs(NP);
+  // the FP64 residual b - A x, and the same in double-float arithmetic on the
+  // FP32 pipes (refined solves on lane-team levels unless the plan asks for FP64)
+  std::vector<MatvecArgs<double>> rss(NP);
+  std::vector<MatvecArgs<dfl>> rds(NP);
+  std::vector<char> dfr(NP);
+  for (int i = 0; i < NP; ++i) {
+    const Level &L = *parts[i].lv;
+    const int b0 = parts[i].b0;
+    MatvecArgs<R> &mv = mvs[i];
+    mv.g = gp[i];
+    mv.B = parts[i].n;
+    mv.T = (C *)w->T + b0 * g.Tsz;
+    mv.D = sizeof(R) == 4 ? (const R *)L.D32 : (const R *)L.D64;
+    mv.Dp = sizeof(R) == 4 ? L.D32p : nullptr;
+    mv.act = k.act + b0;
+    mv.inst = w->inst + b0;
+    mv.iden = sizeof(R) == 4 ? (const R *)(w->iden32 + b0 * g.Nh) : (const R *)(w->iden64 + b0 * g.Nh);
+    mv.tw = sizeof(R) == 4 ? (const C *)p->tw32 : (const C *)p->tw64;
+    mv.xstride = vinst;
+    mv.ystride = vinst;
+    mv.write_back = 0;   // the basis stays unnormalised: pass 1 scales its input by 1 / ||v_j|| on the fly
+    mv.mode = adj ? 2 : 0;
+    mv.form = p->d.form;
+    mv.pc = pcp[i] ? 1 : 0;
+    mv.scale = sizeof(R) == 4 ? (const R *)(k.scale32 + b0) : (const R *)(k.scale64 + b0);
+    MatvecArgs<double> &rs = rss[i];
+    rs.g = gp[i];
+    rs.B = parts[i].n;
+    rs.X = w->x64 + b0 * g.U;
+    rs.xstride = g.U;
+    rs.Y = w->r64 + b0 * g.U;
+    rs.ystride = g.U;
+    rs.T = w->T + b0 * g.Tsz;
+    rs.D = L.D64;
+    rs.act = w->need + b0;
+    rs.inst = w->inst + b0;
+    rs.iden = w->iden64 + b0 * g.Nh;
+    rs.tw = p->tw64;
+    rs.mode = adj ? 3 : 1;
+    rs.form = p->d.form;
+    rs.partial = w->mv_partial + (long long)b0 * w->mvb;
+    rs.counter = w->mv_counter + b0;
+    rs.norm_out = w->mv_norm + b0;
+    dfr[i] = prec && !adj && p->d.residual == GSM_RESID_AUTO && !p->team_only && reg_path_ok(gp[i]) && L.Ddf != nullptr;
+    MatvecArgs<dfl> &rd = rds[i];
+    rd.g = gp[i];
+    rd.B = parts[i].n;
+    rd.X = w->x64 + b0 * g.U;
+    rd.xstride = g.U;
+    rd.Y = w->r64 + b0 * g.U;
+    rd.ystride = g.U;
+    rd.T = reinterpret_cast<dcx *>(w->T) + b0 * g.Tsz;
+    rd.D = L.Ddf;
+    rd.act = w->need + b0;
+    rd.inst = w->inst + b0;
+    rd.iden = w->idendf + b0 * g.Nh;
+    rd.tw = p->twdf;
+    rd.mode = 1;
+    rd.form = p->d.form;
+    rd.partial = w->mv_partial + (long long)b0 * w->mvb;
+    rd.counter = w->mv_counter + b0;
+    rd.norm_out = w->mv_norm + b0;
+    // block sizes of the lane-team kernels: measured on this batch, first use only
+    MatvecArgs<R> tune = mv;
+    tune.X = V + b0 * vinst;
+    tune.Y = tune.X + Us;
+    CK(cudaMemsetAsync(tune.X, 0, (size_t)2 * Us * sizeof(C), st));
+    CK(autotune<R>(p, *parts[i].lv, tune));
+  }
+  MatvecArgs<R> &mv = mvs[0];   // BiCGSTAB (one truncation per batch)
   int outer = 0;
   while (true) {
     bool any = false;
@@ -1063,10 +1159,12 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     // start a Krylov cycle on r (FP64) for every instance that still needs one
     for (int b = 0; b < B; ++b) {
       h_act[b] = need[b];
-      // refined: inner_tol relative to the cycle's residual, but never above
-      // 0.9 tol ||b||, so that a last cycle lands below the target rather than
-      // on it (an instance ending at 1.001 tol costs a whole further cycle)
-      h_thr[b] = prec ? std::min(itol * rnorm[b], 0.9 * tol * bnorm[b]) : 0.5 * tol * bnorm[b];
+      // refined: inner_tol relative to the cycle's residual; a cycle that would
+      // end within 1.5 tol ||b|| (the last one) aims at 0.9 tol ||b||, so that
+      // it lands below the target rather than on it (an instance ending at
+      // 1.001 tol costs a whole further cycle)
+      h_thr[b] = prec ? itol * rnorm[b] : 0.5 * tol * bnorm[b];
+      if (prec && h_thr[b] <= 1.5 * tol * bnorm[b]) h_thr[b] = std::min(h_thr[b], 0.9 * tol * bnorm[b]);
       if (bicg) h_thr[b] *= h_thr[b];   // BiCGSTAB tests ||r||^2
       h_s32[b] = need[b] ? (float)(1.0 / rnorm[b]) : 0.f;
       h_s64[b] = need[b] ? 1.0 / rnorm[b] : 0.0;
@@ -1085,8 +1183,12 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     }
     // V_0 = r in the basis precision (GMRES normalises it in place in the
     // first pass 1; it is BiCGSTAB's r_0 as it stands)
-    CK(launch_start_basis<C>(w->r64, g.U, V, vinst, g.U, B, k.nblk, w->need, st));
-    p->launches++;
+    for (int i = 0; i < NP; ++i) {
+      const int b0 = parts[i].b0;
+      CK(launch_start_basis<C>(w->r64 + b0 * g.U, g.U, V + b0 * vinst, vinst, gp[i].U, parts[i].n, k.nblk,
+                               w->need + b0, st));
+      p->launches++;
+    }
     // complex64 solves keep the correction d (GMRES: in the last basis slot)
     // when the residual will be updated as r -= A d (see below)
     bool recursive = prec && outer > 0;
@@ -1096,11 +1198,11 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     cudaGraphExec_t cyc = nullptr;
     if (bicg) {
       CK(bicg_cycle<R>(p, w, lv, mv, bp, V, vinst, Us, adj, prof, h_act, &cyc));
-      if (pc) CK(launch_sol_update_pc<R>(k, g, w->inst, mv.iden, w->x64, g.U, V, vinst, w->need, -1, BS_D, st, prof));
+      if (pcp[0]) CK(launch_sol_update_pc<R>(k, g, w->inst, mv.iden, w->x64, g.U, V, vinst, w->need, -1, BS_D, st, prof));
       else CK(launch_bicg_sol<R>(w->x64, g.U, V, vinst, bp, w->need, st));
       p->launches++;
     } else {
-    cyc = (p->use_graphs && !prof) ? cycle_graph<R>(p, w, lv, mv, k, V, vinst, Us, adj) : nullptr;
+    cyc = (p->use_graphs && !prof) ? cycle_graph<R>(p, w, parts, mvs, k, V, vinst, Us, adj) : nullptr;
     if (cyc) {
       // the whole cycle on the device: steps run until every instance has
       // converged or the basis is full
@@ -1121,10 +1223,16 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
           for (int b = 0; b < B; ++b) k.nact += h_act[b] != 0;
           if (!k.nact) break;
         }
-        mv.X = V + (long long)j * Us;
-        mv.Y = V + (long long)(j + 1) * Us;
-        mv.nact = prof ? k.nact : 0;
-        CK(matvec<R>(p, lv, mv, prof));
+        for (int i = 0; i < NP; ++i) {
+          MatvecArgs<R> &mi = mvs[i];
+          mi.X = V + parts[i].b0 * vinst + (long long)j * Us;
+          mi.Y = mi.X + Us;
+          mi.nact = 0;
+          if (prof)
+            for (int b = parts[i].b0; b < parts[i].b0 + parts[i].n; ++b) mi.nact += h_act[b] != 0;
+          if (prof && !mi.nact) continue;
+          CK(matvec<R>(p, *parts[i].lv, mi, prof));
+        }
         CK(launch_arnoldi_ortho<R>(k, V, vinst, j, st, prof));
         CK(launch_finish(k, j, st));
         p->launches += 3 + 1 + (k.force_reorth == 2 ? 2 : 4) + 1;   // product, active list, Gram-Schmidt, finish
@@ -1138,40 +1246,56 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
       }
     }
     CK(launch_backsolve(k, st));
-    if (pc)
-      CK(launch_sol_update_pc<R>(k, g, w->inst, mv.iden, w->x64, g.U, V, vinst, w->need, recursive ? m : -1, -1, st,
-                                 prof));
-    else
-      CK(launch_sol_update<R>(k, w->x64, g.U, V, vinst, w->need, recursive ? m : -1, st, prof));
-    p->launches += 2;
+    for (int i = 0; i < NP; ++i) {
+      const int b0 = parts[i].b0;
+      const KrylovPtrs kp = part_ptrs(k, b0, parts[i].n, gp[i].U);
+      if (pcp[i])
+        CK(launch_sol_update_pc<R>(kp, gp[i], w->inst + b0, mvs[i].iden, w->x64 + b0 * g.U, g.U, V + b0 * vinst, vinst,
+                                   w->need + b0, recursive ? m : -1, -1, st, prof));
+      else
+        CK(launch_sol_update<R>(kp, w->x64 + b0 * g.U, g.U, V + b0 * vinst, vinst, w->need + b0, recursive ? m : -1, st,
+                                prof));
+      p->launches++;
+    }
+    p->launches++;
     }
     CK(cudaMemcpyAsync(h_kc, k.kcount, B * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h_dn, k.dnorm2, B * 8, cudaMemcpyDeviceToHost, st));
     if (!recursive) {
       // FP64 residual of the updated iterate
-      if (prof) prof->begin(KIND_RESID64, st);
-      if (df_resid) CK(matvec<dfl>(p, lv, rd, nullptr));
-      else CK(matvec<double>(p, lv, rs, nullptr));
-      if (prof) prof->end(KIND_RESID64, st, 16.0 * B * (double)(2 * g.U + 2 * g.Tsz) + 8.0 * (double)g.L[0] * g.L[1] * g.L[2]);
-      p->launches += 3;
+      for (int i = 0; i < NP; ++i) {
+        const Geo &gi = gp[i];
+        if (prof) prof->begin(KIND_RESID64, st);
+        if (dfr[i]) CK(matvec<dfl>(p, *parts[i].lv, rds[i], nullptr));
+        else CK(matvec<double>(p, *parts[i].lv, rss[i], nullptr));
+        if (prof)
+          prof->end(KIND_RESID64, st,
+                    16.0 * parts[i].n * (double)(2 * gi.U + 2 * gi.Tsz) + 8.0 * (double)gi.L[0] * gi.L[1] * gi.L[2]);
+        p->launches += 3;
+      }
     } else {
       // r -= A d: A d in complex64 has error ~ eps_mv ||A d|| ~ eps_mv ||r_prev||,
       // far below tol ||b|| once a certified ||r|| <= 1e-3 ||b|| (cert_ok).
       // Preconditioned: the slot holds V y and the correction is M^{-1} V y,
       // so A d is the preconditioned product of the slot (md.pc = mv.pc).
-      MatvecArgs<R> md = mv;
-      md.X = V + (long long)(bicg ? (int)BS_D : m) * Us;
-      md.Y = V;
-      md.scale = nullptr;
-      md.write_back = 0;
-      md.mode = adj ? 2 : 0;
-      md.act = w->need;
-      md.nact = 0;
-      for (int b = 0; b < B; ++b) md.nact += need[b] != 0;
-      CK(matvec<R>(p, lv, md, prof));
-      CK(launch_resid_sub(w->r64, g.U, (const float2 *)V, vinst, g.U, B, k.nblk, w->need, w->mv_partial,
-                          w->mv_counter, w->mv_norm, st));
-      p->launches += 4;
+      for (int i = 0; i < NP; ++i) {
+        const int b0 = parts[i].b0;
+        MatvecArgs<R> md = mvs[i];
+        md.X = V + b0 * vinst + (long long)(bicg ? (int)BS_D : m) * Us;
+        md.Y = V + b0 * vinst;
+        md.scale = nullptr;
+        md.write_back = 0;
+        md.mode = adj ? 2 : 0;
+        md.act = w->need + b0;
+        md.nact = 0;
+        for (int b = b0; b < b0 + parts[i].n; ++b) md.nact += need[b] != 0;
+        if (!md.nact) continue;
+        CK(matvec<R>(p, *parts[i].lv, md, prof));
+        CK(launch_resid_sub(w->r64 + b0 * g.U, g.U, (const float2 *)(V + b0 * vinst), vinst, gp[i].U, parts[i].n,
+                            k.nblk, w->need + b0, w->mv_partial + (long long)b0 * k.nblk, w->mv_counter + b0,
+                            w->mv_norm + b0, st));
+        p->launches += 4;
+      }
     }
     CK(cudaMemcpyAsync(h_rn, w->mv_norm, B * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1237,17 +1361,31 @@ static gsm_status solve_batch(gsm_plan_t *p, Level &lv, int B, const gsm_point *
     if (status[b]) worst = (gsm_status)status[b];
   }
   *out_x = w->x64;
+  *out_stride = g.U;
   return worst;
 }
 
-static gsm_status run_group(gsm_plan_t *p, Level &lv, int B, const gsm_point *pts, gsm_info *infos, double2 **x,
-                            bool adj, const double *rhs) {
-  if (p->d.precision == GSM_FP32_REFINE) return solve_batch<float>(p, lv, B, pts, infos, x, adj, rhs);
-  return solve_batch<double>(p, lv, B, pts, infos, x, adj, rhs);
+static gsm_status run_group(gsm_plan_t *p, const std::vector<Part> &parts, int B, const gsm_point *pts,
+                            gsm_info *infos, double2 **x, long long *xs, bool adj, const double *rhs) {
+  if (p->d.precision == GSM_FP32_REFINE) return solve_batch<float>(p, parts, B, pts, infos, x, xs, adj, rhs);
+  return solve_batch<double>(p, parts, B, pts, infos, x, xs, adj, rhs);
 }
 
-// Solve n points grouped by truncation; deliver each instance's field through
-// `sink(point index, level, device field pointer, B-local index)`.
+// A solved batch as the sinks see it: the iterates (x of instance b at
+// x + b xstride) and the batch's split into truncations.
+struct BatchOut {
+  double2 *x;
+  long long xstride;
+  const std::vector<Part> *parts;
+};
+
+// Solve n points; deliver each instance's field through
+// `sink(point index, level, device field pointer, B-local index, batch)`.
+// Points are sorted by truncation; GMRES forward solves put several
+// truncations in one batch (each truncation a contiguous part, the Krylov
+// kernels and the captured inner cycle shared by all), the other solves
+// (BiCGSTAB, adjoint) run one truncation per batch.  GSM_MIXED=0 keeps one
+// truncation per batch everywhere.
 template <typename F>
 static gsm_status solve_points(gsm_plan_t *p, int n, const gsm_point *points, gsm_info *infos, F sink,
                                bool adj = false, const double *rhs = nullptr,
@@ -1260,35 +1398,61 @@ static gsm_status solve_points(gsm_plan_t *p, int n, const gsm_point *points, gs
     if (s) return s;
     groups[Key{{N[0], N[1], N[2]}}].push_back(i);
   }
-  gsm_status worst = GSM_OK;
-  const int Bmax = batch_of(p->d);
+  bool mix = p->d.krylov == GSM_GMRES && !adj && !rhs && groups.size() > 1;
+  if (const char *mx = std::getenv("GSM_MIXED"))
+    if (std::strcmp(mx, "0") == 0) mix = false;
+  // the points in truncation order, each with its level
+  std::vector<int> order;
+  std::vector<Level *> lvl;
   for (auto &kv : groups) {
     Level *lv;
     gsm_status s = get_level(p, kv.first.N, &lv);
     if (s) return s;
-    const std::vector<int> &idx = kv.second;
-    for (size_t off = 0; off < idx.size(); off += Bmax) {
-      const int B = (int)std::min<size_t>(Bmax, idx.size() - off);
-      std::vector<gsm_point> pts(B);
-      std::vector<gsm_info> inf(B);
-      std::vector<double> r6(rhs ? 6 * B : 0);
-      for (int b = 0; b < B; ++b) {
-        pts[b] = points[idx[off + b]];
-        if (rhs)
-          for (int i = 0; i < 6; ++i) r6[6 * b + i] = rhs[6 * (size_t)idx[off + b] + i];
-      }
-      double2 *x = nullptr;
-      s = run_group(p, *lv, B, pts.data(), inf.data(), &x, adj, rhs ? r6.data() : nullptr);
-      if (s && s != GSM_ERR_NOCONV) return s;
-      if (s) worst = s;
-      for (int b = 0; b < B; ++b) {
-        if (infos) infos[idx[off + b]] = inf[b];
-        s = sink(idx[off + b], *lv, x + (size_t)b * lv->g.U, b, x);
-        if (s) return s;
-      }
-      // before the next batch reuses the workspace
-      if (batch_end && (s = batch_end())) return s;
+    for (int i : kv.second) {
+      order.push_back(i);
+      lvl.push_back(lv);
     }
+  }
+  gsm_status worst = GSM_OK;
+  const int Bmax = batch_of(p->d);
+  size_t off = 0;
+  while (off < order.size()) {
+    // the next batch: up to Bmax points, across truncations only when mixing
+    size_t end = std::min(order.size(), off + (size_t)Bmax);
+    if (!mix)
+      for (size_t e = off + 1; e < end; ++e)
+        if (lvl[e] != lvl[off]) {
+          end = e;
+          break;
+        }
+    const int B = (int)(end - off);
+    std::vector<Part> parts;
+    for (int b = 0; b < B; ++b) {
+      if (parts.empty() || parts.back().lv != lvl[off + b]) parts.push_back(Part{lvl[off + b], b, 0});
+      parts.back().n++;
+    }
+    std::vector<gsm_point> pts(B);
+    std::vector<gsm_info> inf(B);
+    std::vector<double> r6(rhs ? 6 * B : 0);
+    for (int b = 0; b < B; ++b) {
+      pts[b] = points[order[off + b]];
+      if (rhs)
+        for (int i = 0; i < 6; ++i) r6[6 * b + i] = rhs[6 * (size_t)order[off + b] + i];
+    }
+    double2 *x = nullptr;
+    long long xs = 0;
+    gsm_status s = run_group(p, parts, B, pts.data(), inf.data(), &x, &xs, adj, rhs ? r6.data() : nullptr);
+    if (s && s != GSM_ERR_NOCONV) return s;
+    if (s) worst = s;
+    const BatchOut bo{x, xs, &parts};
+    for (int b = 0; b < B; ++b) {
+      if (infos) infos[order[off + b]] = inf[b];
+      s = sink(order[off + b], *lvl[off + b], x + (size_t)b * xs, b, bo);
+      if (s) return s;
+    }
+    // before the next batch reuses the workspace
+    if (batch_end && (s = batch_end())) return s;
+    off = end;
   }
   return worst;
 }
@@ -1389,6 +1553,7 @@ void gsm_plan_destroy(gsm_plan_t *p) {
   cudaFree(p->tw32);
   cudaFree(p->twdf);
   if (p->pin) cudaFreeHost(p->pin);
+  cudaFree(p->e0_dev);
   delete p;
 }
 
@@ -1592,7 +1757,7 @@ gsm_status gsm_solve(gsm_plan_t *p, int n, const gsm_point *points, double *E, i
   };
   gsm_status s = solve_points(
       p, n, points, infos,
-      [&](int i, Level &lv, double2 *xf, int, double2 *) -> gsm_status {
+      [&](int i, Level &lv, double2 *xf, int, const BatchOut &) -> gsm_status {
         const size_t bytes = lv.g.U * 16;
         if (run_bytes && (double *)((char *)run_dst + run_bytes) == E + 2 * off[i] &&
             (const double2 *)((const char *)run_src + run_bytes) == xf) {
@@ -1616,14 +1781,27 @@ gsm_status gsm_sweep(gsm_plan_t *p, int n, const gsm_point *points, double *E0, 
   if (!p) return GSM_ERR_ARG;
   if (!E0) return fail(p, GSM_ERR_ARG, "E0 is NULL");
   cudaSetDevice(p->d.device);
-  gsm_status s = solve_points(p, n, points, infos, [&](int i, Level &lv, double2 *, int b, double2 *x) -> gsm_status {
+  // E_0 of every instance of a batch, gathered on the device at its first
+  // instance (per truncation), then one small copy per point
+  std::vector<double2> e0;
+  gsm_status s = solve_points(p, n, points, infos, [&](int i, Level &, double2 *, int b, const BatchOut &bo) -> gsm_status {
     if (b == 0) {
-      // gather E_0 of the whole batch once, at its first instance
-      Work &w = p->works[Key{{lv.g.N[0], lv.g.N[1], lv.g.N[2]}}];
-      CK(launch_extract_e0(x, lv.g.U, lv.g, w.B, w.e0, p->st));
+      const std::vector<Part> &parts = *bo.parts;
+      const int B = parts.back().b0 + parts.back().n;
+      if (p->e0_cap < B) {
+        cudaFree(p->e0_dev);
+        p->e0_dev = nullptr;
+        p->e0_cap = 0;
+        if (cudaMalloc(&p->e0_dev, (size_t)B * 48) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(p, GSM_ERR_NOMEM, "E_0 staging allocation failed");
+        }
+        p->e0_cap = B;
+      }
+      for (const Part &q : parts)
+        CK(launch_extract_e0(bo.x + (size_t)q.b0 * bo.xstride, bo.xstride, q.lv->g, q.n, p->e0_dev + 3 * q.b0, p->st));
     }
-    Work &w = p->works[Key{{lv.g.N[0], lv.g.N[1], lv.g.N[2]}}];
-    CK(cudaMemcpyAsync(E0 + 6 * (size_t)i, w.e0 + 3 * b, 48, cudaMemcpyDeviceToHost, p->st));
+    CK(cudaMemcpyAsync(E0 + 6 * (size_t)i, p->e0_dev + 3 * b, 48, cudaMemcpyDeviceToHost, p->st));
     return GSM_OK;
   });
   if (s && s != GSM_ERR_NOCONV) return s;
@@ -1787,7 +1965,7 @@ static gsm_status adjoint_impl(gsm_plan_t *p, int n, const gsm_point *points, co
   }
   gsm_status worst = GSM_OK;
   // forward fields
-  s = solve_points(p, n, points, nullptr, [&](int i, Level &, double2 *xf, int, double2 *) -> gsm_status {
+  s = solve_points(p, n, points, nullptr, [&](int i, Level &, double2 *xf, int, const BatchOut &) -> gsm_status {
     CK(cudaMemcpyAsync(Ef + (size_t)i * g.U, xf, g.U * 16, cudaMemcpyDeviceToDevice, st));
     return GSM_OK;
   });
@@ -1797,10 +1975,10 @@ static gsm_status adjoint_impl(gsm_plan_t *p, int n, const gsm_point *points, co
   // adjoint fields and their correlation with the forward ones
   s = solve_points(
       p, n, points, nullptr,
-      [&](int i, Level &lvl, double2 *lam, int b, double2 *) -> gsm_status {
+      [&](int i, Level &lvl, double2 *lam, int b, const BatchOut &) -> gsm_status {
         Work &w = p->works[Key{{lvl.g.N[0], lvl.g.N[1], lvl.g.N[2]}}];
         CK(cudaMemsetAsync(grid, 0, (size_t)6 * LL * 16, st));
-        CK(launch_adj_scatter(g, lam, Ef + (size_t)i * g.U, w.inst + b, w.iden64 + (size_t)b * g.Nh, grid, st));
+        CK(launch_adj_scatter(g, lam, Ef + (size_t)i * g.U, w.inst + b, w.iden64 + (size_t)b * g.ist, grid, st));
         CK(launch_fft_axis(grid, g.L[0], g.L[1], g.L[2], 0, +1, 6, LL, p->tw64, st));
         CK(launch_fft_axis(grid, g.L[0], g.L[1], g.L[2], 1, +1, 6, LL, p->tw64, st));
         CK(launch_fft_axis(grid, g.L[0], g.L[1], g.L[2], 2, +1, 6, LL, p->tw64, st));

@@ -108,6 +108,11 @@ struct Geo {
   long long Nh;    // N0 N1 N2
   long long U;     // 3 Nh complex unknowns per instance
   long long Tsz;   // 3 L0 N1 N2: per-instance intermediate of the matvec
+  // per-instance strides of the intermediate T and of the per-harmonic
+  // arrays (1/(k_m^2 - k_b^2)): Tsz and Nh for a batch of one truncation, the
+  // largest box's sizes when truncations share a batch
+  long long Tst;
+  long long ist;
 };
 
 // cyclic position of harmonic index i (0..N-1, m = i - n) on an L-point grid

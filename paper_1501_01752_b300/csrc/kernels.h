@@ -156,6 +156,9 @@ struct KrylovPtrs {
   double *dnorm2;           // [B] ||d||^2 of the correction added to x by the last solution update
   double *dpartial;         // [B][nblk] its block partials (shared with the product's norm partials)
   unsigned *dcounter;       // [B] its last-block counters
+  long long *ulen;          // [B] stored length of each instance's vectors (U_b rounded up to 64), for
+                            // batches of several truncations; the vector stride stays Us.
+                            // Uniform batches pass nullptr to the kernels (every length Us)
   double *svec;             // [B][m+1] 1 / ||v_i|| of every stored basis vector: GMRES keeps the
                             // basis unnormalised (v_i = svec_i * V_i), the scales enter the dots,
                             // the update coefficients and the solution update

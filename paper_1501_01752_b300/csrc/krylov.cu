@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
                                              const int *__restrict__ gate, double *partial, unsigned *counter,
                                              double *out, int ostride, int nblk, const int *__restrict__ jdev,
                                              const int *__restrict__ alist, int bcap,
-                                             const double *__restrict__ svec, int sstride) {
+                                             const double *__restrict__ svec, int sstride,
+                                             const long long *__restrict__ ulen) {
   using C = typename Cx<R>::T;
   constexpr int EPT = EptDots<R>::v, NW = KT / 32, CH = 4, NA = 2 * GV + 1;
   __shared__ double wsum[NA][NW];
@@ -67,13 +68,14 @@ __global__ void __launch_bounds__(KT) k_dots(const typename Cx<R>::T *__restrict
   const C *Vb = V + b * vinst;
   const C *W = Vb + (long long)wi * Us;
   const C *V0 = Vb + (long long)i0 * Us;
-  const long long ntiles = (Us + KT * EPT - 1) / (KT * EPT);
+  const long long Ub = ulen ? ulen[b] : Us;   // this instance's stored length (vectors stay Us apart)
+  const long long ntiles = (Ub + KT * EPT - 1) / (KT * EPT);
   R acc[NA];
 #pragma unroll
   for (int k = 0; k < NA; ++k) acc[k] = 0;
   for (long long t = blk; ng > 0 && t < ntiles; t += nblk) {
     const long long e0 = t * (KT * EPT) + (long long)threadIdx.x * EPT;
-    if (e0 >= Us) continue;          // Us is a multiple of 64: a thread's EPT values are all in range
+    if (e0 >= Ub) continue;          // Ub is a multiple of 64: a thread's EPT values are all in range
     C w[EPT];
     load_ept<C, EPT>(w, W + e0);
     if (grp == 0)
@@ -160,7 +162,8 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
                                                double *partial, unsigned *counter, double *wn_out,
                                                int *gate_out, int force, const int *__restrict__ jdev,
                                                const int *__restrict__ alist, int nblk, int bcap,
-                                               const double *__restrict__ svec, int sstride) {
+                                               const double *__restrict__ svec, int sstride,
+                                               const long long *__restrict__ ulen) {
   using C = typename Cx<R>::T;
   constexpr int EPT = Ept<R>::v;
   if (jdev) {
@@ -186,11 +189,12 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
   __syncthreads();
   C *Vb = V + b * vinst;
   C *W = Vb + (long long)wi * Us;
-  const long long ntiles = (Us + KT * EPT - 1) / (KT * EPT);
+  const long long Ub = ulen ? ulen[b] : Us;
+  const long long ntiles = (Ub + KT * EPT - 1) / (KT * EPT);
   double acc = 0;
   for (long long t = blk; t < ntiles; t += nblk) {
     const long long e0 = t * (KT * EPT) + (long long)threadIdx.x * EPT;
-    if (e0 >= Us) continue;
+    if (e0 >= Ub) continue;
     C w[EPT];
     load_ept<C, EPT>(w, W + e0);
     int i = 0;
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
     const R kx = (R)(inst[b].kinc[0] + (mx - g.n[0]) * g.K[0]);
     const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
     const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
-    const R al = rcp((R)1 - pcc * iden[(long long)b * Nh + e]);
+    const R al = rcp((R)1 - pcc * iden[(long long)b * g.ist + e]);
     const R k2 = kx * kx + ky * ky + kz * kz;
     const R f = k2 > (R)0 ? (pcb - al) * rcp(k2) : (R)0;
     const R kr = kx * d[0].x + ky * d[1].x + kz * d[2].x, ki = kx * d[0].y + ky * d[1].y + kz * d[2].y;
@@ -589,20 +593,20 @@ cudaError_t launch_arnoldi_ortho(const KrylovPtrs &k, typename Cx<R>::T *V, long
   const double vb = (double)sizeof(typename Cx<R>::T) * k.U * (k.nact > 0 ? k.nact : k.B);
   if (prof) prof->begin(KIND_DOTS, st);
   k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, nullptr, k.partial, k.counter, k.hdot0, hs, k.nblk, k.jdev,
-                                    k.alist, k.bcap, k.svec, k.m + 1);
+                                    k.alist, k.bcap, k.svec, k.m + 1, k.ulen);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot0, hs, k.act, nullptr, k.partial, k.counter, k.wn0,
-                                   k.gate, k.force_reorth, k.jdev, k.alist, k.nblk, k.bcap, k.svec, k.m + 1);
+                                   k.gate, k.force_reorth, k.jdev, k.alist, k.nblk, k.bcap, k.svec, k.m + 1, k.ulen);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   if (k.force_reorth == 2) return cudaGetLastError();   // no second pass: gate was cleared
   if (prof) prof->begin(KIND_DOTS, st);
   k_dots<R><<<gdots, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.act, k.gate, k.partial, k.counter, k.hdot1, hs, k.nblk, k.jdev,
-                                    k.alist, k.bcap, k.svec, k.m + 1);
+                                    k.alist, k.bcap, k.svec, k.m + 1, k.ulen);
   if (prof) prof->end(KIND_DOTS, st, vb * (nv + 1));
   if (prof) prof->begin(KIND_UPDATE, st);
   k_update<R><<<grid, KT, 0, st>>>(V, vinst, k.Us, nv, wi, k.hdot1, hs, k.act, k.gate, k.partial, k.counter, k.wn1,
-                                   nullptr, 0, k.jdev, k.alist, k.nblk, k.bcap, k.svec, k.m + 1);
+                                   nullptr, 0, k.jdev, k.alist, k.nblk, k.bcap, k.svec, k.m + 1, k.ulen);
   if (prof) prof->end(KIND_UPDATE, st, vb * (nv + 2));
   return cudaGetLastError();
 }

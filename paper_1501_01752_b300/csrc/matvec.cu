@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
   const int mz = blockIdx.x / nchunk, my0 = (blockIdx.x % nchunk) * rows;
   const int nr = min(rows, N1 - my0);
   C *Xb = X + b * xstride;
-  C *Tb = T + b * g.Tsz;
+  C *Tb = T + b * g.Tst;
   const R s = scale ? scale[b] : (R)1;
   const long long Nh = g.Nh;
   Team tm(g.L[0]);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
           const C kv = mk(kx * v0.x + ky * v1.x + kz * v2.x, kx * v0.y + ky * v1.y + kz * v2.y);
           const R kc = c == 0 ? kx : (c == 1 ? ky : kz);
           const C vc = c == 0 ? v0 : (c == 1 ? v1 : v2);
-          const R id = iden[b * Nh + h];
+          const R id = iden[b * g.ist + h];
           v = mk(id * (kb2 * vc.x - kc * kv.x), id * (kb2 * vc.y - kc * kv.y));
         } else {
           // (k x v)_c
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_yz(Geo g, typen
   const int rx = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   if (act && !act[b]) return;
   load_twiddles(tw, twg);
-  C *Tb = T + b * g.Tsz + ((long long)rx * 3 + c) * N2 * N1;
+  C *Tb = T + b * g.Tst + ((long long)rx * 3 + c) * N2 * N1;
   for (int e = threadIdx.x; e < N2 * P1; e += blockDim.x) A[e] = czero<C>();
   __syncthreads();
   for (int e = threadIdx.x; e < N2 * N1; e += blockDim.x) {
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
   load_twiddles(tw, twg);
   const int mz = blockIdx.x / nchunk, my0 = (blockIdx.x % nchunk) * rows;
   const int nr = min(rows, N1 - my0);
-  const C *Tb = T + b * g.Tsz;
+  const C *Tb = T + b * g.Tst;
   const long long Nh = g.Nh;
   for (int c = 0; c < 3; ++c)
     for (int e = threadIdx.x; e < nr * L0; e += blockDim.x) {
@@ -213,14 +213,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
     const int px = wrap(mx, g.n[0], L0);
     C u0 = S[(0 * rows + row) * P0 + px], u1 = S[(1 * rows + row) * P0 + px], u2 = S[(2 * rows + row) * P0 + px];
     if (HF) {
-      const R kx = kxs[mx], ky = kys[row], id = iden[b * Nh + h];
+      const R kx = kxs[mx], ky = kys[row], id = iden[b * g.ist + h];
       const C w0 = csub(cscale(u2, ky), cscale(u1, kz)), w1 = csub(cscale(u0, kz), cscale(u2, kx)),
               w2 = csub(cscale(u1, kx), cscale(u0, ky));
       u0 = cscale(w0, id);
       u1 = cscale(w1, id);
       u2 = cscale(w2, id);
     } else if (!(MODE & 2)) {
-      const R kx = kxs[mx], ky = kys[row], id = iden[b * Nh + h];
+      const R kx = kxs[mx], ky = kys[row], id = iden[b * g.ist + h];
       const C ku = mk(kx * u0.x + ky * u1.x + kz * u2.x, kx * u0.y + ky * u1.y + kz * u2.y);
       u0 = mk(id * (kb2 * u0.x - kx * ku.x), id * (kb2 * u0.y - kx * ku.y));
       u1 = mk(id * (kb2 * u1.x - ky * ku.x), id * (kb2 * u1.y - ky * ku.y));
@@ -254,9 +254,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x(Geo g, co
 // ------------------------------------------------ 1/(k_m^2 - k_b^2) tables
 __global__ void k_iden(Geo g, const Inst *__restrict__ inst, int B, double *id64, float *id32, dfl *iddf) {
   const long long tot = (long long)B * g.Nh;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e / g.Nh);
-    long long h = e - (long long)b * g.Nh;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / g.Nh);
+    long long h = t - (long long)b * g.Nh;
+    const long long e = (long long)b * g.ist + h;
     const int mx = (int)(h % g.N[0]);
     h /= g.N[0];
     const int my = (int)(h % g.N[1]);

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
     int my, mz;
     const int plane = divmod_small(r, N1, rN1, my);
     const int c = divmod_small(plane, N2, rN2, mz);
-    C *Tq = T + b * g.Tsz + ((3 * F::freq(ln.lane, 0) + c) * P + mz * N1 + my);
+    C *Tq = T + b * g.Tst + ((3 * F::freq(ln.lane, 0) + c) * P + mz * N1 + my);
 #pragma unroll
     for (int q = 0; q < 8; ++q) Tq[F::fstep(q) * 3 * P] = v[i][q];
   }
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
   const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
   const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
   IO *Xr = X + b * xstride + r * N0;
-  const R *idr = iden ? iden + (long long)b * Nh + r * N0 : nullptr;
+  const R *idr = iden ? iden + (long long)b * g.ist + r * N0 : nullptr;
   const R pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
   C v[3][8];
 #pragma unroll
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
     v[1][a] = csub(cscale(u[0], kz), cscale(u[2], kx));
     v[2][a] = csub(cscale(u[1], kx), cscale(u[0], ky));
   }
-  C *Tq = T + b * g.Tsz + (3 * F::freq(ln.lane, 0) * P + mz * N1 + my);
+  C *Tq = T + b * g.Tst + (3 * F::freq(ln.lane, 0) * P + mz * N1 + my);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     F::template forward<+1>(v[c], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
   const int rx = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   if (act && !act[b]) return;
   const int N1 = g.N[1], N2 = g.N[2];
-  C *Tp = T + b * g.Tsz + ((long long)rx * 3 + c) * N2 * N1;   // [m_z][m_y] block
+  C *Tp = T + b * g.Tst + ((long long)rx * 3 + c) * N2 * N1;   // [m_z][m_y] block
   // y forward: team per m_z row, straight from global memory
   {
     const Lanes ln(FY::TS);
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, c
   const int N1 = g.N[1], N2 = g.N[2];
   const int xp = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   if (act && !act[b]) return;
-  float2 *Ta = T + b * g.Tsz + ((long long)(2 * xp) * 3 + c) * N2 * N1;   // [m_z][m_y] block of r_x = 2 xp
+  float2 *Ta = T + b * g.Tst + ((long long)(2 * xp) * 3 + c) * N2 * N1;   // [m_z][m_y] block of r_x = 2 xp
   float2 *Tb = Ta + 3LL * N2 * N1;                                         // and of r_x = 2 xp + 1
   const int team = threadIdx.x >> 3, lane = threadIdx.x & 7;
   const unsigned mask = 0xffu << (threadIdx.x & 24);
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, 
   const int N1 = g.N[1], N2 = g.N[2];
   const int xp = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   if (act && !act[b]) return;
-  float2 *Ta = T + b * g.Tsz + ((long long)(2 * xp) * 3 + c) * N2 * N1;   // [m_z][m_y] block of r_x = 2 xp
+  float2 *Ta = T + b * g.Tst + ((long long)(2 * xp) * 3 + c) * N2 * N1;   // [m_z][m_y] block of r_x = 2 xp
   float2 *Tb = Ta + 3LL * N2 * N1;                                         // and of r_x = 2 xp + 1
   const int team = threadIdx.x >> 3, lane = threadIdx.x & 7;
   const unsigned mask = 0xffu << (threadIdx.x & 24);
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
         px[i][m][0] = io_in<C>(Xb[h]);
         px[i][m][1] = io_in<C>(Xb[Nh + h]);
         px[i][m][2] = io_in<C>(Xb[2 * Nh + h]);
-        pid[i][m] = iden[(long long)b * Nh + h];
+        pid[i][m] = iden[(long long)b * g.ist + h];
       }
     }
   for (int i = threadIdx.x; i < N0; i += blockDim.x) kxs[i] = (R)(inst[b].kinc[0] + (i - g.n[0]) * g.K[0]);
@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       it_c[i] = c;
       it_row[i] = row;
       const bool valid = c < 3 && row < nr;
-      const C *Tq = T + b * g.Tsz + ((3 * F::freq(ln.lane, 0) + c) * P2 + r0 + row);
+      const C *Tq = T + b * g.Tst + ((3 * F::freq(ln.lane, 0) + c) * P2 + r0 + row);
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[i][q] = valid ? Tq[F::fstep(q) * 3 * P2] : mk((R)0, (R)0);
     }
@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       const int mx = wl + 32 * m;
       if (mx < N0) {
         const int h = (r0 + row) * N0 + mx;
-        body(row, mx, io_in<C>(Xb[h]), io_in<C>(Xb[Nh + h]), io_in<C>(Xb[2 * Nh + h]), iden[(long long)b * Nh + h]);
+        body(row, mx, io_in<C>(Xb[h]), io_in<C>(Xb[Nh + h]), io_in<C>(Xb[2 * Nh + h]), iden[(long long)b * g.ist + h]);
       }
     }
   if (norm_out) last_block_sum((double)acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);

@@ -88,3 +88,46 @@ def test_bench_configuration_batch_512_sampled_by_oracle():
     F = E.reshape(512, -1)
     for b in (0, 137, 300, 511):
         assert _oracle_residual(st, n_harm, 1.0, pts[b], F[b]) <= 1.2e-8, b
+
+
+def _c3_points(per_class=20):
+    st = wl.ellipsoid_lattice(period=1.0)
+    pts = []
+    for gi, N in enumerate((15, 21, 31)):
+        k0 = 2 * math.pi * (0.2 + 0.05 * gi)
+        for j in range(per_class):
+            p = wl.point((1.04 + 0.01 * j) * k0, (0, 0, 1), (1, 0, 0) if j % 2 else (0, 1, 0), k0)
+            p["n_harm"] = (N, N, N)
+            pts.append(p)
+    return st, pts
+
+
+@pytest.mark.parametrize("precision", ["c64_refine", "fp64"])
+@pytest.mark.parametrize("graphs", ["1", "0"])
+def test_batches_across_truncations_match_one_truncation_batches(precision, graphs, monkeypatch):
+    # 60 points of truncations 15/21/31 in batches of 32: mixed batches (the
+    # truncations share the Krylov kernels and the captured inner cycle)
+    # against one-truncation batches (GSM_MIXED=0), and the oracle's residual
+    monkeypatch.setenv("GSM_GRAPHS", graphs)
+    monkeypatch.setenv("GSM_BLOCKS", "256,256,256")
+    g = gsm()
+    st, pts = _c3_points()
+    fp64 = precision == "fp64"
+    tol = 1e-11 if fp64 else 1e-8
+    out = {}
+    for mixed in ("1", "0"):
+        monkeypatch.setenv("GSM_MIXED", mixed)
+        plan = g.plan_for(st, (31, 31, 31), precision=g.FP64 if fp64 else g.FP32_REFINE, tol=tol, max_batch=32)
+        E, infos, s = plan.solve(pts)
+        plan.close()
+        assert s == 0 and all(i["rel_residual"] <= tol for i in infos)
+        out[mixed] = E
+    off = 0
+    for b, p in enumerate(pts):
+        N = p["n_harm"]
+        U = 3 * N[0] * N[1] * N[2]
+        Em, Eg = out["1"][off:off + U], out["0"][off:off + U]
+        assert rel(Em, Eg) < (1e-9 if fp64 else 1e-6), (b, rel(Em, Eg))
+        if b % 7 == 0:
+            assert _oracle_residual(st, N, 1.0, p, Em) <= 1.5 * tol, b
+        off += U
