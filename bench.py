@@ -52,7 +52,7 @@ OWN_MV_PC = OWN_MV + 4 * N_HARM[0] ** 3
 # product launch at the bench batch (512 instances), from one ncu capture of
 # the current kernels, per operator; None where no capture of the current
 # kernels exists.
-NCU_TRAFFIC = {"precond": None, "plain": None}
+NCU_TRAFFIC = {"precond": 4.1299e9, "plain": 4.0508e9}
 # FP64 work of one FP64 product of one instance on this grid, from one ncu
 # count of the three FP64 product kernels at 32 instances: floating-point
 # operations (2 DFMA + DADD + DMUL) and FP64-pipe instructions (DFMA + DADD +
@@ -391,9 +391,10 @@ def main():
                 "own_layout_GBps": own, "own_layout_frac": own / peak,
                 "traffic_over_own_layout": None if traffic is None else traffic / (B * own_bytes + 4 * L_FFT ** 3)}
 
-    roof = product_roofline(args.precond != "none", OWN_MV_PC if args.precond != "none" else OWN_MV,
-                            "roofline_product")
-    roof_plain = product_roofline(False, OWN_MV, "roofline_product_plain") if args.precond != "none" else None
+    # the preconditioner exists for Eq. 4 only: an Eq. 5 solve iterates with the plain operator
+    pc_solve = args.precond != "none" and args.form == "e"
+    roof = product_roofline(pc_solve, OWN_MV_PC if pc_solve else OWN_MV, "roofline_product")
+    roof_plain = product_roofline(False, OWN_MV, "roofline_product_plain") if pc_solve else None
     # Gram-Schmidt passes (dots + update) inside the profiled solve, at the
     # algorithmic bytes of the instances still iterating at each step
     kr_ms = kinds["krylov_dots"][1] + kinds["krylov_update"][1]

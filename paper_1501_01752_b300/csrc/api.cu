@@ -695,7 +695,6 @@ static cudaError_t autotune(gsm_plan_t *p, Level &lv, const MatvecArgs<R> &base)
   MatvecArgs<R> a = base;
   a.yzv = p->yzv;
   a.scale = nullptr;
-  a.write_back = 0;
   a.act = nullptr;
   a.norm_out = nullptr;
   a.mode = 0;
@@ -867,7 +866,6 @@ static cudaError_t bicg_cycle(gsm_plan_t *p, Work *w, const Level &lv, const Mat
   cudaStream_t st = p->st;
   MatvecArgs<R> mv = mv0;
   mv.scale = nullptr;
-  mv.write_back = 0;
   mv.jdev = nullptr;
   mv.mode = adj ? 2 : 0;
   cudaError_t e = launch_bicg_step<R>(BICG_INIT, bp, V, vinst, st);
@@ -1101,7 +1099,6 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
     mv.tw = sizeof(R) == 4 ? (const C *)p->tw32 : (const C *)p->tw64;
     mv.xstride = vinst;
     mv.ystride = vinst;
-    mv.write_back = 0;   // the basis stays unnormalised: pass 1 scales its input by 1 / ||v_j|| on the fly
     mv.mode = adj ? 2 : 0;
     mv.form = p->d.form;
     mv.pc = pcp[i] ? 1 : 0;
@@ -1284,7 +1281,6 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
         md.X = V + b0 * vinst + (long long)(bicg ? (int)BS_D : m) * Us;
         md.Y = V + b0 * vinst;
         md.scale = nullptr;
-        md.write_back = 0;
         md.mode = adj ? 2 : 0;
         md.act = w->need + b0;
         md.nact = 0;

@@ -78,6 +78,20 @@ template <int S, typename C> __device__ __forceinline__ void dft8(C* v) {
   v[7] = csub(e3, t3);
 }
 
+// outputs 0, 1, 6, 7 of the 8-point DFT above (the others are left
+// undefined): the last stage of an inverse lane-team transform, whose
+// outputs outside the harmonic box are not kept
+template <int S, typename C> __device__ __forceinline__ void dft8_out0167(C* v) {
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<S>(e0, e1, e2, e3);
+  dft4<S>(o0, o1, o2, o3);
+  v[0] = cadd(e0, o0);
+  v[1] = cadd(e1, rot8<S>(o1));
+  v[6] = csub(e2, mul_si<S>(o2));
+  v[7] = csub(e3, rot8_3<S>(o3));
+}
+
 // 3-point DFT: with w = exp(S 2 pi i / 3) = -1/2 + S i sqrt(3)/2,
 // X0 = v0 + v1 + v2, X1,2 = v0 - (v1 + v2)/2 +- S i (sqrt(3)/2) (v1 - v2)
 template <int S, typename C> __device__ __forceinline__ void dft3(C* v) {

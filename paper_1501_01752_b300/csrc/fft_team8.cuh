@@ -148,7 +148,9 @@ template <int L> struct Team8 {
     __syncwarp(mask);
   }
 
-  template <int S, typename C>
+  // OUT0167: only the natural positions lane + TS a with a in {0, 1, 6, 7}
+  // are computed (every harmonic position of a grid with L >= 4 n + 4)
+  template <int S, bool OUT0167 = false, typename C>
   __device__ static __forceinline__ void inverse(C (&v)[8], int lane, const C (&w)[NTW], C *buf, unsigned mask) {
     if constexpr (TS == 16) {
       const int p = lane >> 1, t1 = lane & 1;
@@ -166,7 +168,8 @@ template <int L> struct Team8 {
       __syncwarp(mask);
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] = buf[lane * 9 + q];   // G'[q][t = lane]
-      dft8<S>(v);                                   // x[lane + 16 a], a = register
+      if (OUT0167) dft8_out0167<S>(v);
+      else dft8<S>(v);                              // x[lane + 16 a], a = register
       __syncwarp(mask);
       return;
     }
@@ -199,7 +202,8 @@ template <int L> struct Team8 {
 #pragma unroll
       for (int p = 0; p < 8; ++p) v[p] = buf[p * 9 + lane];   // W[p][t = lane]
     }
-    dft8<S>(v);                                               // x[lane + TS a], a = register
+    if (OUT0167) dft8_out0167<S>(v);
+    else dft8<S>(v);                                          // x[lane + TS a], a = register
     __syncwarp(mask);
   }
 

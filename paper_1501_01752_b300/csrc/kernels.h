@@ -81,7 +81,6 @@ template <typename R> struct MatvecArgs {
   const R *D = nullptr;    // convolution multiplier [rx][ry][rz]
   const float2 *Dp = nullptr;  // complex64 only: D as x-plane pairs [rx / 2][ry][rz] (nullptr = unpaired pass 2)
   const R *scale = nullptr;  // per-instance input scale (nullptr = 1)
-  int write_back = 0;      // write the scaled input back to X (normalises a Krylov vector)
   const int *act = nullptr;
   const Inst *inst = nullptr;
   const R *iden = nullptr; // [B][Nh] 1/(k_m^2 - k_b^2)

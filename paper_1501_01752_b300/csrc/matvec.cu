@@ -30,8 +30,8 @@ template <typename C> __device__ __forceinline__ C czero() { C z; z.x = 0; z.y =
 // PRE 0: the input as it is (Eq. 4); PRE 1: G(m) x first (adjoint of Eq. 4);
 // PRE 2: k_m x x first (Eq. 5, H-field formulation)
 template <typename R, int PRE>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, typename Cx<R>::T *__restrict__ X, long long xstride,
-                        typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale, int write_back,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, const typename Cx<R>::T *__restrict__ X, long long xstride,
+                        typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
                         const int *__restrict__ act, const Inst *__restrict__ inst,
                         const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg, int rows,
                         int nchunk, const int *__restrict__ jdev, long long jstride) {
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2], L0 = g.L[0], P0 = L0 + 1;
   const int mz = blockIdx.x / nchunk, my0 = (blockIdx.x % nchunk) * rows;
   const int nr = min(rows, N1 - my0);
-  C *Xb = X + b * xstride;
+  const C *Xb = X + b * xstride;
   C *Tb = T + b * g.Tst;
   const R s = scale ? scale[b] : (R)1;
   const long long Nh = g.Nh;
@@ -68,7 +68,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
       C v;
       if (PRE == 0) {
         v = cscale(Xb[c * Nh + h], s);
-        if (write_back) Xb[c * Nh + h] = v;
       } else {
         const R kx = (R)(inst[b].kinc[0] + (mx - g.n[0]) * g.K[0]);
         const R ky = (R)(inst[b].kinc[1] + (my0 + row - g.n[1]) * g.K[1]);
@@ -96,13 +95,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_fwd_x(Geo g, ty
       Tb[(((long long)rx * 3 + c) * N2 + mz) * N1 + my0 + row] = S[row * P0 + rx];
     }
     __syncthreads();
-  }
-  if (PRE && write_back) {
-    for (int e = threadIdx.x; e < nr * N0; e += blockDim.x) {
-      const int row = e / N0, mx = e - row * N0;
-      const long long h = ((long long)mz * N1 + my0 + row) * N0 + mx;
-      for (int c = 0; c < 3; ++c) Xb[c * Nh + h] = cscale(Xb[c * Nh + h], s);
-    }
   }
 }
 
@@ -320,7 +312,7 @@ cudaError_t launch_matvec(const MatvecArgs<R> &a, cudaStream_t st, Profiler *pro
     if (prof) prof->begin(KIND_FWD_X, st);
 #define GSM_P1(PRE)                                                                                       \
   cudaFuncSetAttribute(k_fwd_x<R, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
-  k_fwd_x<R, PRE><<<grid, threads, smem, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst, \
+  k_fwd_x<R, PRE><<<grid, threads, smem, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.inst, \
                                                a.iden, a.tw, rows, nchunk, a.jdev, a.jstride)
     if (a.mode & 2) { GSM_P1(1); }
     else if (a.form) { GSM_P1(2); }

@@ -82,9 +82,9 @@ template <int L, int TS> struct HarmSlots {
 // them before the first transform, so that more reads are in flight per
 // thread.  Row indices are 32-bit (3 N1 N2 < 2^22 rows per instance).
 template <typename R, int L0, int TT, int RPT>
-__global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__restrict__ X, long long xstride,
+__global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, const typename Io<R>::T *__restrict__ X, long long xstride,
                                                  typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
-                                                 int write_back, const int *__restrict__ act,
+                                                 const int *__restrict__ act,
                                                  const typename Cx<R>::T *__restrict__ twg, const int *__restrict__ jdev,
                                                  long long jstride) {
   using C = typename Cx<R>::T;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
   const HarmSlots<L0, TS> hs(ln.lane, g.n[0]);
   const int rbase = blockIdx.x * RB * RPT + ln.team;
   const R s = scale ? scale[b] : (R)1;
-  IO *Xb = X + b * xstride;
+  const IO *Xb = X + b * xstride;
   C v[RPT][8];
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
@@ -128,14 +128,6 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
       v[i][a].x *= s;
       v[i][a].y *= s;
     }
-    if (write_back && valid) {
-      IO *Xr = Xb + r * N0;
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int j = HarmSlots<L0, TS>::slot(a);
-        if (j >= 0 && hs.off[j] >= 0) Xr[hs.off[j]] = io_out<IO>(v[i][a]);
-      }
-    }
     F::template forward<+1>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
     if (!valid) continue;
     int my, mz;
@@ -155,9 +147,9 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, typename Io<R>::T *__res
 // G(m) x (the adjoint of Eq. 4, A^H v = v - T (G v): G is real and symmetric
 // for real k and k_b, and T Hermitian for real eps).
 template <typename R, int L0, int TT>
-__global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__restrict__ X, long long xstride,
+__global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, const typename Io<R>::T *__restrict__ X, long long xstride,
                                                   typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
-                                                  int write_back, const int *__restrict__ act,
+                                                  const int *__restrict__ act,
                                                   const Inst *__restrict__ inst,
                                                   const typename Cx<R>::T *__restrict__ twg, const int *__restrict__ jdev,
                                                   long long jstride, int op, const R *__restrict__ iden) {
@@ -182,7 +174,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
   const int mz = divmod_small(r, N1, 1.0f / (float)N1, my);
   const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
   const R kz = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
-  IO *Xr = X + b * xstride + r * N0;
+  const IO *Xr = X + b * xstride + r * N0;
   const R *idr = iden ? iden + (long long)b * g.ist + r * N0 : nullptr;
   const R pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
   C v[3][8];
@@ -205,9 +197,6 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, typename Io<R>::T *__re
     C u[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[c] = mk(v[c][a].x * s, v[c][a].y * s);
-    if (write_back && valid && h >= 0)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Xr[c * Nh + h] = io_out<IO>(u[c]);
     if constexpr (!std::is_same<R, dfl>::value) {
       if (op == 1) {
         // M^{-1} u = alpha u + (beta - alpha) k (k . u) / k^2 (zero where no harmonic sits)
@@ -316,7 +305,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
           v[q] = cscale(v[q], Dc[FZ::freq(ln.lane, q)]);
         }
       }
-      FZ::template inverse<-1>(v, ln.lane, w, bf, ln.mask);
+      FZ::template inverse<-1, true>(v, ln.lane, w, bf, ln.mask);
       if (valid)
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
@@ -337,7 +326,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8(Geo g, typename Cx<R>::T *__restri
       C v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] = valid ? A[yz_at<LY>(mz, FY::freq(ln.lane, q))] : mk((R)0, (R)0);
-      FY::template inverse<-1>(v, ln.lane, w, bufs + ln.team * FY::BUF, ln.mask);
+      FY::template inverse<-1, true>(v, ln.lane, w, bufs + ln.team * FY::BUF, ln.mask);
       if (valid)
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
@@ -654,7 +643,7 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     const HarmSlots<L0, TS> hs(ln.lane, g.n[0]);
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-      F::template inverse<-1>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
+      F::template inverse<-1, true>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
       if (it_c[i] < 3 && it_row[i] < nr) {
         C *Sr = S3 + (it_c[i] * rows + it_row[i]) * P;
 #pragma unroll
@@ -771,13 +760,13 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
     constexpr int TX = tt128<R, TT>();
     if (a.form || a.pc || a.mode >= 2) {
       dim3 gridh((int)(((long long)g.N[2] * g.N[1] + TX / 16 - 1) / (TX / 16)), a.B);
-      k_fwd_x_t8h<R, 128, TX><<<gridh, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
+      k_fwd_x_t8h<R, 128, TX><<<gridh, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.inst,
                                                     a.tw, a.jdev, a.jstride, a.form ? 0 : (a.mode >= 2 ? 2 : 1),
                                                     a.iden);
     } else {
       const int RB = TX / 16 * P1_RPT;
       dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
-      k_fwd_x_t8<R, 128, TX, P1_RPT><<<grid, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act,
+      k_fwd_x_t8<R, 128, TX, P1_RPT><<<grid, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act,
                                                           a.tw, a.jdev, a.jstride);
     }
     return;
@@ -789,18 +778,18 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
     const int op = a.form ? 0 : (a.mode >= 2 ? 2 : 1);
     dim3 gridh((int)(((long long)g.N[2] * g.N[1] + RBH - 1) / RBH), a.B);
     if (g.L[0] == 64)
-      k_fwd_x_t8h<R, 64, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
+      k_fwd_x_t8h<R, 64, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.inst,
                                                    a.tw, a.jdev, a.jstride, op, a.iden);
     else
-      k_fwd_x_t8h<R, 32, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.inst,
+      k_fwd_x_t8h<R, 32, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.inst,
                                                    a.tw, a.jdev, a.jstride, op, a.iden);
     return;
   }
   if (g.L[0] == 64)
-    k_fwd_x_t8<R, 64, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw,
+    k_fwd_x_t8<R, 64, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.tw,
                                                        a.jdev, a.jstride);
   else
-    k_fwd_x_t8<R, 32, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.write_back, a.act, a.tw,
+    k_fwd_x_t8<R, 32, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.tw,
                                                        a.jdev, a.jstride);
 }
 
@@ -934,7 +923,7 @@ cudaError_t launch_matvec_reg(const MatvecArgs<R> &a, cudaStream_t st, Profiler 
   const bool p1h = a.form || a.pc || a.mode >= 2;
   if (prof)
     prof->end(KIND_FWD_X, st,
-              nb * (cs * (double)(g.U + g.Tsz + (a.write_back ? g.U : 0)) + (p1h ? sizeof(R) * (double)g.Nh : 0.0)));
+              nb * (cs * (double)(g.U + g.Tsz) + (p1h ? sizeof(R) * (double)g.Nh : 0.0)));
   if (prof) prof->begin(KIND_YZ, st);
   if ((e = launch_reg_pass<R>(2, t2, a, st)) != cudaSuccess) return e;
   if (prof) prof->end(KIND_YZ, st, nb * 2.0 * cs * (double)g.Tsz + sizeof(R) * (double)g.L[0] * g.L[1] * g.L[2]);
