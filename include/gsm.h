@@ -260,7 +260,10 @@ gsm_status gsm_level_fft(const gsm_plan_t *plan, const int n_harm[3], int fft_ou
  * pairs (fma.rn.f32x2).  One wave of 256-thread blocks per SM slot, eight
  * independent chains per thread, best of five launches timed with CUDA
  * events on cuda_stream (NULL = default stream); *tflops = 2 x FMAs / s.
- * Allocates and frees a small result buffer; changes no device setting. */
+ * Allocates and frees a small result buffer; changes no device setting.
+ * GSM_ERR_ARG for a null tflops or another kind, GSM_ERR_CUDA if the device
+ * cannot be selected or a launch fails, GSM_ERR_NOMEM if the buffer cannot
+ * be allocated. */
 gsm_status gsm_probe_fma(int device, void *cuda_stream, int kind, double *tflops);
 
 const char *gsm_last_error(const gsm_plan_t *plan);
