@@ -1069,6 +1069,9 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
   // since the last certified residual: the rounding error of those updates
   // is at most EPS_MV_C64 times it
   std::vector<double> dsum(B, 0.0);
+  // instances whose recursive residual met the target but could not certify
+  // it: they need the certified residual b - A x, not another Krylov cycle
+  std::vector<char> verify(B, 0);
   for (int b = 0; b < B; ++b) {
     double s2 = 0;
     for (int i = 0; i < 6; ++i) s2 += hI[b].a[i] * hI[b].a[i];
@@ -1153,20 +1156,71 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
     CK(autotune<R>(p, *parts[i].lv, tune));
   }
   MatvecArgs<R> &mv = mvs[0];   // BiCGSTAB (one truncation per batch)
+  // the certified residual r = b - A x of the instances flagged in w->need
+  // (double-float product on lane-team levels, else FP64), ||r||^2 in mv_norm
+  auto certify = [&]() -> gsm_status {
+    for (int i = 0; i < NP; ++i) {
+      const Geo &gi = gp[i];
+      if (prof) prof->begin(KIND_RESID64, st);
+      if (dfr[i]) CK(matvec<dfl>(p, *parts[i].lv, rds[i], nullptr));
+      else CK(matvec<double>(p, *parts[i].lv, rss[i], nullptr));
+      if (prof)
+        prof->end(KIND_RESID64, st,
+                  16.0 * parts[i].n * (double)(2 * gi.U + 2 * gi.Tsz) + 8.0 * (double)gi.L[0] * gi.L[1] * gi.L[2]);
+      p->launches += 3;
+    }
+    return GSM_OK;
+  };
   int outer = 0;
   while (true) {
-    bool any = false;
-    for (int b = 0; b < B; ++b) any |= need[b] != 0;
+    bool any = false, verify_only = true;
+    for (int b = 0; b < B; ++b) {
+      any |= need[b] != 0;
+      if (need[b] && !verify[b]) verify_only = false;
+    }
     if (!any) break;
+    if (verify_only) {
+      // every remaining instance only needs its residual certified
+      for (int b = 0; b < B; ++b) h_act[b] = need[b];
+      CK(cudaMemcpyAsync(w->need, h_act, B * 4, cudaMemcpyHostToDevice, st));
+      const gsm_status cs = certify();
+      if (cs != GSM_OK) return cs;
+      CK(cudaMemcpyAsync(h_rn, w->mv_norm, B * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int b = 0; b < B; ++b) {
+        if (!need[b]) continue;
+        verify[b] = 0;
+        dsum[b] = 0.0;
+        rnorm[b] = std::sqrt(std::max(h_rn[b], 0.0));
+        cert_ok[b] = rnorm[b] <= 1e-3 * bnorm[b];
+        if (!std::isfinite(rnorm[b])) {
+          need[b] = 0;
+          status[b] = GSM_ERR_NOCONV;
+        } else if (rnorm[b] <= tol * bnorm[b]) {
+          need[b] = 0;
+        }
+      }
+      if (const char *dbg = std::getenv("GSM_DEBUG")) {
+        if (std::atoi(dbg) >= 2) {
+          int live = 0;
+          for (int b = 0; b < B; ++b) live += need[b];
+          std::fprintf(stderr, "gsm: certified check only, still %d\n", live);
+        }
+      }
+      continue;
+    }
     // start a Krylov cycle on r (FP64) for every instance that still needs one
     for (int b = 0; b < B; ++b) {
       h_act[b] = need[b];
       // refined: inner_tol relative to the cycle's residual; a cycle that would
       // end within 1.5 tol ||b|| (the last one) aims at 0.9 tol ||b||, so that
-      // it lands below the target rather than on it (an instance ending at
-      // 1.001 tol costs a whole further cycle)
+      // it lands below the target rather than on it, and no cycle aims below
+      // 0.5 tol ||b||: one that starts just above the target (the last cycle's
+      // residual ended there, the Givens estimate being off by the basis's
+      // loss of orthogonality) needs a step or two, not inner_tol below it
       h_thr[b] = prec ? itol * rnorm[b] : 0.5 * tol * bnorm[b];
       if (prec && h_thr[b] <= 1.5 * tol * bnorm[b]) h_thr[b] = std::min(h_thr[b], 0.9 * tol * bnorm[b]);
+      if (prec) h_thr[b] = std::max(h_thr[b], 0.5 * tol * bnorm[b]);
       if (bicg) h_thr[b] *= h_thr[b];   // BiCGSTAB tests ||r||^2
       h_s32[b] = need[b] ? (float)(1.0 / rnorm[b]) : 0.f;
       h_s64[b] = need[b] ? 1.0 / rnorm[b] : 0.0;
@@ -1264,17 +1318,9 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
     CK(cudaMemcpyAsync(h_kc, k.kcount, B * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h_dn, k.dnorm2, B * 8, cudaMemcpyDeviceToHost, st));
     if (!recursive) {
-      // FP64 residual of the updated iterate
-      for (int i = 0; i < NP; ++i) {
-        const Geo &gi = gp[i];
-        if (prof) prof->begin(KIND_RESID64, st);
-        if (dfr[i]) CK(matvec<dfl>(p, *parts[i].lv, rds[i], nullptr));
-        else CK(matvec<double>(p, *parts[i].lv, rss[i], nullptr));
-        if (prof)
-          prof->end(KIND_RESID64, st,
-                    16.0 * parts[i].n * (double)(2 * gi.U + 2 * gi.Tsz) + 8.0 * (double)gi.L[0] * gi.L[1] * gi.L[2]);
-        p->launches += 3;
-      }
+      // FP64-accurate residual of the updated iterate
+      const gsm_status cs = certify();
+      if (cs != GSM_OK) return cs;
     } else {
       // r -= A d: A d in complex64 has error ~ eps_mv ||A d|| ~ eps_mv ||r_prev||,
       // far below tol ||b|| once a certified ||r|| <= 1e-3 ||b|| (cert_ok).
@@ -1329,6 +1375,8 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
         status[b] = GSM_ERR_NOCONV;
       } else if (rnorm[b] <= tol * bnorm[b] && trusted) {
         need[b] = 0;
+      } else if (rnorm[b] <= tol * bnorm[b]) {
+        verify[b] = 1;   // met the target on an untrusted recursive residual
       } else if (iters[b] >= max_it || steps[b] >= 200) {
         need[b] = 0;
         status[b] = GSM_ERR_NOCONV;
