@@ -993,13 +993,17 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
   // complex64 inner solves of Eq. 4 stop at inner_tol >= 1e-6, far above the
   // level (~1e-7 relative) where classical Gram-Schmidt without
   // reorthogonalisation loses orthogonality, so they skip the second pass.
-  // Eq. 5 keeps the DGKS test: without it the basis of its complex64 cycles
-  // loses orthogonality early, the Givens estimate runs ahead of the true
-  // residual (a cycle aimed at 1e-4 reached 2e-3) and the refined woodpile
-  // solves took 90 products and 2.9 refinement steps against 37 and 2 with
-  // it.  FP64 solves keep the test.  GSM_REORTH = 0 (test) / 1 (always) /
-  // 2 (never) overrides.
-  k.force_reorth = (prec && inner_tol_of(p->d) >= 1e-6 && p->d.form == GSM_FORM_E) ? 2 : 0;
+  // The complex64 cycles of Eq. 5 lose it early without one (the Givens
+  // estimate runs ahead of the true residual: a cycle aimed at 1e-4 reached
+  // 2e-3, and the refined woodpile solves took 90 products and 2.9
+  // refinement steps against 37 and 2).  The DGKS test fires at every one
+  // of their steps; a second pass at every fourth step keeps the same 37
+  // products and 2 steps for 1.25 passes per step instead of 2 (every sixth:
+  // 37.7 products; every eighth: 46).  FP64 solves keep the test.
+  // GSM_REORTH = 0 (test) / 1 (always) / 2 (never) / k >= 3 (every (k - 1)-th
+  // step) overrides.
+  k.force_reorth = 0;
+  if (prec && inner_tol_of(p->d) >= 1e-6) k.force_reorth = p->d.form == GSM_FORM_E ? 2 : 5;
   if (const char *ro = std::getenv("GSM_REORTH")) k.force_reorth = std::atoi(ro);
   // BiCGSTAB scalars live in the GMRES per-instance arrays (gv has room for 4
   // complex values per instance, partial for 3 sums per block)

@@ -14,8 +14,9 @@
 // reorthogonalisation test instead of the paper's modified Gram-Schmidt: the
 // j sequential dot/axpy pairs of MGS become two fused passes (four when the
 // test fires), with orthogonality at least as good as MGS.  The test can be
-// forced on or off per solve (force 1 / 2): complex64 inner solves, which
-// stop at 1e-4 relative, skip the second pass.  Dots of FP32 vectors sum
+// forced on or off per solve (force 1 / 2), or replaced by a second pass at
+// every (force - 1)-th step (force >= 3): complex64 inner solves of Eq. 4,
+// which stop at 1e-4 relative, skip the second pass.  Dots of FP32 vectors sum
 // FP32 products in each thread's registers and across a warp, and the warp
 // sums in FP64; Hessenberg, rotations and residual estimates are FP64.
 // Reductions across blocks use the last-block-done pattern (atomic counter,
@@ -225,7 +226,8 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
   if (last_block_sum(acc, red, partial + (long long)a * nblk, counter + b, wn_out + b, 0, nblk, blk)) {
     if (gate_out && threadIdx.x == 0) {
       const double before = h[(long long)b * hstride + 2 * nv];
-      gate_out[b] = (force == 1 || (force == 0 && wn_out[b] < 0.5 * before)) ? 1 : 0;
+      gate_out[b] = (force == 1 || (force == 0 && wn_out[b] < 0.5 * before) ||
+                     (force >= 3 && nv % (force - 1) == 0)) ? 1 : 0;
     }
   }
 }
