@@ -999,11 +999,16 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
   // refinement steps against 37 and 2).  The DGKS test fires at every one
   // of their steps; a second pass at every fourth step keeps the same 37
   // products and 2 steps for 1.25 passes per step instead of 2 (every sixth:
-  // 37.7 products; every eighth: 46).  FP64 solves keep the test.
-  // GSM_REORTH = 0 (test) / 1 (always) / 2 (never) / k >= 3 (every (k - 1)-th
-  // step) overrides.
-  k.force_reorth = 0;
-  if (prec && inner_tol_of(p->d) >= 1e-6) k.force_reorth = p->d.form == GSM_FORM_E ? 2 : 5;
+  // 37.7 products; every eighth: 46).  FP64 solves to tol >= 1e-10 take the
+  // same rule: the DGKS test fired at every step there too, and the woodpile
+  // batch needs the same 32.8 products with a pass at every fourth step
+  // (179 -> 216 solves/s; 232 with none, kept as a margin for long cycles
+  // near poles).  Tighter FP64 solves keep the test: at tol 1e-13 the basis
+  // between periodic passes is not orthogonal enough to reach the target.
+  // GSM_REORTH = 0 (test) / 1 (always) / 2 (never) / k >= 3 (every
+  // 2^(k - 2)-th step) overrides.
+  if (prec) k.force_reorth = (inner_tol_of(p->d) >= 1e-6 && p->d.form == GSM_FORM_E) ? 2 : 4;
+  else k.force_reorth = tol_of(p->d) >= 1e-10 ? 4 : 0;
   if (const char *ro = std::getenv("GSM_REORTH")) k.force_reorth = std::atoi(ro);
   // BiCGSTAB scalars live in the GMRES per-instance arrays (gv has room for 4
   // complex values per instance, partial for 3 sums per block)

@@ -162,7 +162,7 @@ struct KrylovPtrs {
                             // basis unnormalised (v_i = svec_i * V_i), the scales enter the dots,
                             // the update coefficients and the solution update
   double *resid;            // [B]
-  int force_reorth;         // 0: DGKS test, 1: always reorthogonalise, 2: never, k >= 3: every (k - 1)-th step
+  int force_reorth;         // 0: DGKS test, 1: always reorthogonalise, 2: never, k >= 3: every 2^(k - 2)-th step
   int nact;                 // profiling only: instances active in the step launched (0 = all B);
                             // the recorded bytes of the Gram-Schmidt passes count these
   int *jdev;                // graph mode: Arnoldi step counter on the device (nullptr: host j)

@@ -15,8 +15,9 @@
 // j sequential dot/axpy pairs of MGS become two fused passes (four when the
 // test fires), with orthogonality at least as good as MGS.  The test can be
 // forced on or off per solve (force 1 / 2), or replaced by a second pass at
-// every (force - 1)-th step (force >= 3): complex64 inner solves of Eq. 4,
-// which stop at 1e-4 relative, skip the second pass.  Dots of FP32 vectors sum
+// every 2^(force - 2)-th step (force >= 3; a power of two, so that the test
+// costs the kernel no registers): complex64 inner solves of Eq. 4, which
+// stop at 1e-4 relative, skip the second pass.  Dots of FP32 vectors sum
 // FP32 products in each thread's registers and across a warp, and the warp
 // sums in FP64; Hessenberg, rotations and residual estimates are FP64.
 // Reductions across blocks use the last-block-done pattern (atomic counter,
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(KT) k_update(typename Cx<R>::T *__restrict__ V
     if (gate_out && threadIdx.x == 0) {
       const double before = h[(long long)b * hstride + 2 * nv];
       gate_out[b] = (force == 1 || (force == 0 && wn_out[b] < 0.5 * before) ||
-                     (force >= 3 && nv % (force - 1) == 0)) ? 1 : 0;
+                     (force >= 3 && (nv & ((1 << (force - 2)) - 1)) == 0)) ? 1 : 0;
     }
   }
 }
