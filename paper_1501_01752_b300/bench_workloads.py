@@ -114,7 +114,7 @@ def sweep_c3(args):
     st = wl.ellipsoid_lattice(period=1.0)
     f = 4 * math.pi / 3 * 0.4 * 0.3 * 0.2
     n_mg = math.sqrt(_mg(6.0, 1.0, f))
-    mb = getattr(args, "sweep_batch", 128)
+    mb = getattr(args, "sweep_batch", 256)
     plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=mb, precond=_pc(args))
     pts, groups = [], []
     for gi in range(16):
