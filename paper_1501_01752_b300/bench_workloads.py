@@ -106,16 +106,15 @@ def sweep(args):
     print(json.dumps(sweep_c3(args)), flush=True)
 
 
-def sweep_c3(args):
-    """The C3 resonance sweep of the retrieval, timed: one gsm_sweep call over
-    512 points of truncations 15/21/31 (batches of sweep_batch points, which
-    may span truncations), then the 32 pole fits on the host.  Returns the
-    result as a dict."""
+def c3_points():
+    """The C3 resonance sweep's points: the ellipsoid lattice (eps 6, Lambda
+    = 1), 16 frequencies k0 Lambda / 2 pi = 0.10 ... 0.40 with truncations
+    15/21/31 in turn, 16 kappa across each resonance window, x and y
+    polarisation along z.  Returns (structure, points, groups, n_MG); each
+    group is (ratio, polarisation, kappa values, point indices, k0)."""
     st = wl.ellipsoid_lattice(period=1.0)
     f = 4 * math.pi / 3 * 0.4 * 0.3 * 0.2
     n_mg = math.sqrt(_mg(6.0, 1.0, f))
-    mb = getattr(args, "sweep_batch", 256)
-    plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=mb, precond=_pc(args))
     pts, groups = [], []
     for gi in range(16):
         ratio = 0.10 + 0.02 * gi
@@ -131,6 +130,17 @@ def sweep_c3(args):
                 idx.append(len(pts))
                 pts.append(p)
             groups.append((ratio, pol, kap, idx, k0))
+    return st, pts, groups, n_mg
+
+
+def sweep_c3(args):
+    """The C3 resonance sweep of the retrieval, timed: gsm_sweep over the 512
+    points of c3_points() (batches of sweep_batch points, which may span
+    truncations), then the 32 pole fits on the host.  Returns the result as
+    a dict."""
+    st, pts, groups, n_mg = c3_points()
+    mb = getattr(args, "sweep_batch", 256)
+    plan = gsm.plan_for(st, (31, 31, 31), precision=gsm.FP32_REFINE, tol=1e-8, max_batch=mb, precond=_pc(args))
     plan.sweep(pts[:64])                          # warm-up (plan levels, workspaces)
     torch.cuda.synchronize()
     # the whole sweep five times (each call solves all 512 points from

@@ -102,3 +102,4 @@ def test_bicgstab_reports_only_certified_convergence(pole):
                 assert i["rel_residual"] <= tol and r <= 1.5 * tol, (i, r)
             else:
                 assert i["status"] == g.GSM_ERR_NOCONV, i
+
