@@ -190,8 +190,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=512,
-                    help="points per batched solve (measured on one B300: 32: 2834, 64: 3186, 128: 3457, "
-                         "256: 3596, 512: 3853, 1024: 3547 solves/s)")
+                    help="points per batched solve (measured on one B300: 128: 3685, 256: 3877, 512: 4165-4174, "
+                         "1024: 4204 solves/s)")
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--alt-steps", type=int, default=5,
@@ -207,6 +207,8 @@ def main():
                     help="outer-residual arithmetic of the refined solve (double-float where available, or FP64)")
     ap.add_argument("--precond", default="auto", choices=["auto", "none"],
                     help="averaged-medium right preconditioner of the Krylov solves (auto) or none")
+    ap.add_argument("--mv-batch", type=int, default=32,
+                    help="instances per product of the matvec workload")
     ap.add_argument("--sweep-batch", type=int, default=256,
                     help="instances per batch of the sweep workload (batches span truncations; measured on one "
                          "B300, solves/s: 64: 6097, 128: 6761, 256: 7309, 512: 7071)")

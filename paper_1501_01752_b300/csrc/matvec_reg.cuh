@@ -178,14 +178,17 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, const typename Io<R>::T
   const R *idr = iden ? iden + (long long)b * g.ist + r * N0 : nullptr;
   const R pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
   C v[3][8];
+  R idv[4];   // 1/(k_m^2 - k_b^2) of the four harmonic slots, loaded with x (op 1, 2)
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const int j = HarmSlots<L0, TS>::slot(a);
 #pragma unroll
     for (int c = 0; c < 3; ++c) v[c][a] = mk((R)0, (R)0);
+    if (j >= 0) idv[j] = (R)0;
     if (j >= 0 && valid && hs.off[j] >= 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) v[c][a] = io_in<C>(Xr[c * Nh + hs.off[j]]);
+      if (op == 1 || op == 2) idv[j] = idr[hs.off[j]];
     }
   }
 #pragma unroll
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, const typename Io<R>::T
       if (op == 1) {
         // M^{-1} u = alpha u + (beta - alpha) k (k . u) / k^2 (zero where no harmonic sits)
         if (!valid || h < 0) continue;
-        const R al = rcp((R)1 - pcc * idr[h]);
+        const R al = rcp((R)1 - pcc * idv[j]);
         const R k2 = kx * kx + ky * ky + kz * kz;
         const R f = k2 > (R)0 ? (pcb - al) * rcp(k2) : (R)0;
         const C ku = mk(kx * u[0].x + ky * u[1].x + kz * u[2].x, kx * u[0].y + ky * u[1].y + kz * u[2].y);
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, const typename Io<R>::T
       if (op == 2) {
         // G u = (k_b^2 u - k (k . u)) / (k_m^2 - k_b^2) (zero where no harmonic sits)
         if (!valid || h < 0) continue;
-        const R id = idr[h], kb2 = (R)inst[b].kb2;
+        const R id = idv[j], kb2 = (R)inst[b].kb2;
         const C ku = mk(kx * u[0].x + ky * u[1].x + kz * u[2].x, kx * u[0].y + ky * u[1].y + kz * u[2].y);
         v[0][a] = mk(id * (kb2 * u[0].x - kx * ku.x), id * (kb2 * u[0].y - kx * ku.y));
         v[1][a] = mk(id * (kb2 * u[1].x - ky * ku.x), id * (kb2 * u[1].y - ky * ku.y));
