@@ -52,7 +52,7 @@ OWN_MV_PC = OWN_MV + 4 * N_HARM[0] ** 3
 # product launch at the bench batch (512 instances), from one ncu capture of
 # the current kernels, per operator; None where no capture of the current
 # kernels exists.
-NCU_TRAFFIC = {"precond": 4.1302e9, "plain": 4.0533e9}
+NCU_TRAFFIC = {"precond": 4.1347e9, "plain": 4.0548e9}
 # FP64 work of one FP64 product of one instance on this grid, from one ncu
 # count of the three FP64 product kernels at 32 instances: floating-point
 # operations (2 DFMA + DADD + DMUL) and FP64-pipe instructions (DFMA + DADD +
