@@ -216,15 +216,19 @@ namespace gsm {
 struct Team8x2R {
   static constexpr int L = 64;
 
-  // per lane t: tw[r] = w^{t ((r + t) mod 8)} (r < 8) and md[j] = w8^{a t}
-  // for a = 1, 6, 7 (j = 0, 1, 2), from the positive-sign table
-  __device__ static __forceinline__ void constants(WP (&tw)[8], WP (&md)[3], int t, const float2 *twg) {
+  // per lane t: tw[r] = w^{t ((r + t) mod 8)} (r < 8), from the
+  // positive-sign table
+  __device__ static __forceinline__ void constants(WP (&tw)[8], int t, const float2 *twg) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const float2 x = __ldg(&twg[((t * ((r + t) & 7)) & 63) * (TWN / L)]);
       tw[r].c = make_float2(x.x, x.x);
       tw[r].s = make_float2(x.y, x.y);
     }
+  }
+  // the same and md[j] = w8^{a t} for a = 1, 6, 7 (j = 0, 1, 2)
+  __device__ static __forceinline__ void constants(WP (&tw)[8], WP (&md)[3], int t, const float2 *twg) {
+    constants(tw, t, twg);
     const int as[3] = {1, 6, 7};
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -247,13 +251,17 @@ struct Team8x2R {
     }
   }
 
-  // forward of inputs whose registers 2..5 are zero; phase-deferred output
-  template <int S>
-  __device__ static __forceinline__ void forward(CP (&v)[8], int t, const WP (&tw)[8], const WP (&md)[3],
+  // forward of inputs whose registers 2..5 are zero; phase-deferred output.
+  // MOD = false: the caller has already multiplied x[t + 8 a] by w8^{S a t}
+  // (md is not read)
+  template <int S, bool MOD = true>
+  __device__ static __forceinline__ void forward(CP (&v)[8], int t, const WP (&tw)[8], const WP *md,
                                                  unsigned mask) {
-    v[1] = cp_twiddle<S>(v[1], md[0]);
-    v[6] = cp_twiddle<S>(v[6], md[1]);
-    v[7] = cp_twiddle<S>(v[7], md[2]);
+    if constexpr (MOD) {
+      v[1] = cp_twiddle<S>(v[1], md[0]);
+      v[6] = cp_twiddle<S>(v[6], md[1]);
+      v[7] = cp_twiddle<S>(v[7], md[2]);
+    }
     Team8x2::dft8_in0167<S>(v);
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = cp_twiddle<S>(v[r], tw[r]);
@@ -262,18 +270,21 @@ struct Team8x2R {
   }
 
   // inverse of a phase-deferred input; natural outputs at a in {0, 1, 6, 7}
-  // only (the others are left undefined)
-  template <int S>
-  __device__ static __forceinline__ void inverse(CP (&v)[8], int t, const WP (&tw)[8], const WP (&md)[3],
+  // only (the others are left undefined).  MOD = false leaves the factor
+  // w8^{S a t} of output x[t + 8 a] to the caller (md is not read).
+  template <int S, bool MOD = true>
+  __device__ static __forceinline__ void inverse(CP (&v)[8], int t, const WP (&tw)[8], const WP *md,
                                                  unsigned mask) {
     Team8x2::dft8<S>(v);
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = cp_twiddle<S>(v[r], tw[r]);
     rotate_exchange(v, t, mask);
     Team8x2::dft8_out0167<-S>(v);
-    v[1] = cp_twiddle<S>(v[1], md[0]);
-    v[6] = cp_twiddle<S>(v[6], md[1]);
-    v[7] = cp_twiddle<S>(v[7], md[2]);
+    if constexpr (MOD) {
+      v[1] = cp_twiddle<S>(v[1], md[0]);
+      v[6] = cp_twiddle<S>(v[6], md[1]);
+      v[7] = cp_twiddle<S>(v[7], md[2]);
+    }
   }
 };
 

@@ -30,6 +30,16 @@ __device__ __forceinline__ int harm_at(int k, int n, int L) {
   return -1;
 }
 
+// Index k of the factor w8^k = exp(2 pi i k / 8) that the shuffle yz pass
+// (k_yz_t8x2r) leaves to passes 1 and 3 for the T row of harmonic indices
+// (hy, hz) on the 64-point y and z grids: with grid positions p = (h - n) mod
+// 64 = t + 8 a, k = (a_y t_y + a_z t_z) mod 8 (the rotation's input
+// modulations along y and z; its inverses take the conjugate).
+__device__ __forceinline__ int yz_phase_index(int hy, int ny, int hz, int nz) {
+  const int py = (hy - ny) & 63, pz = (hz - nz) & 63;
+  return ((py >> 3) * (py & 7) + (pz >> 3) * (pz & 7)) & 7;
+}
+
 constexpr int TB_DEFAULT = 256;  // threads per block unless the autotuner picks another
 
 struct Lanes {
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, const typename Io<R>::T 
                                                  typename Cx<R>::T *__restrict__ T, const R *__restrict__ scale,
                                                  const int *__restrict__ act,
                                                  const typename Cx<R>::T *__restrict__ twg, const int *__restrict__ jdev,
-                                                 long long jstride) {
+                                                 long long jstride, int ph) {
   using C = typename Cx<R>::T;
   using IO = typename Io<R>::T;
   using F = Team8<L0>;
@@ -123,16 +133,24 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8(Geo g, const typename Io<R>::T 
   for (int i = 0; i < RPT; ++i) {
     const int r = rbase + i * RB;
     const bool valid = r < nrows;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      v[i][a].x *= s;
-      v[i][a].y *= s;
-    }
-    F::template forward<+1>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
-    if (!valid) continue;
     int my, mz;
     const int plane = divmod_small(r, N1, rN1, my);
     const int c = divmod_small(plane, N2, rN2, mz);
+    if (ph) {   // the scale times the row's factor for the shuffle yz pass
+      const C wk = ldg_c(&twg[yz_phase_index(my, g.n[1], mz, g.n[2]) * (TWN / 8)]);
+      const C sw = mk(wk.x * s, wk.y * s);
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        if (HarmSlots<L0, TS>::slot(a) >= 0) v[i][a] = cmul(v[i][a], sw);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        v[i][a].x *= s;
+        v[i][a].y *= s;
+      }
+    }
+    F::template forward<+1>(v[i], ln.lane, w, bufs + ln.team * F::BUF, ln.mask);
+    if (!valid) continue;
     C *Tq = T + b * g.Tst + ((3 * F::freq(ln.lane, 0) + c) * P + mz * N1 + my);
 #pragma unroll
     for (int q = 0; q < 8; ++q) Tq[F::fstep(q) * 3 * P] = v[i][q];
@@ -152,7 +170,7 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, const typename Io<R>::T
                                                   const int *__restrict__ act,
                                                   const Inst *__restrict__ inst,
                                                   const typename Cx<R>::T *__restrict__ twg, const int *__restrict__ jdev,
-                                                  long long jstride, int op, const R *__restrict__ iden) {
+                                                  long long jstride, int op, const R *__restrict__ iden, int ph) {
   using C = typename Cx<R>::T;
   using IO = typename Io<R>::T;
   using F = Team8<L0>;
@@ -190,6 +208,16 @@ __global__ void __launch_bounds__(TT) k_fwd_x_t8h(Geo g, const typename Io<R>::T
       for (int c = 0; c < 3; ++c) v[c][a] = io_in<C>(Xr[c * Nh + hs.off[j]]);
       if (op == 1 || op == 2) idv[j] = idr[hs.off[j]];
     }
+  }
+  if (ph) {
+    // the row's factor for the shuffle yz pass: a complex constant per row
+    // commutes with every per-harmonic map below
+    const C wk = ldg_c(&twg[yz_phase_index(my, g.n[1], mz, g.n[2]) * (TWN / 8)]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (HarmSlots<L0, TS>::slot(a) >= 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c][a] = cmul(v[c][a], wk);
   }
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -469,7 +497,12 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2(Geo g, float2 *__restrict__ T, c
 // only the plane.  The y forward leaves its rows phase-deferred (frequency
 // r_y carries the factor w8^{-(r_y mod 8)(r_y / 8)}, constant along each z
 // column); the z forward, x D, z inverse of a column keep that factor, and
-// the y inverse consumes it, so T is left exactly as by k_yz_t8x2.
+// the y inverse consumes it.  The rotation's input modulations w8^{a t} (y
+// position t + 8 a) and w8^{a' t'} (z position t' + 8 a') are a factor per
+// (m_z, m_y) row of T, which pass 1 applies to its output (yz_phase_index)
+// and pass 3 removes from its input, and so are the conjugate output
+// modulations of the inverses: T between the passes is the plain
+// intermediate times that factor, and this kernel never applies it.
 template <int TT>
 __global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, const float2 *__restrict__ Dp,
                                                  const int *__restrict__ act, const float2 *__restrict__ twg) {
@@ -484,8 +517,8 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, 
   float2 *Tb = Ta + 3LL * N2 * N1;                                         // and of r_x = 2 xp + 1
   const int team = threadIdx.x >> 3, lane = threadIdx.x & 7;
   const unsigned mask = 0xffu << (threadIdx.x & 24);
-  WP tw[8], md[3];
-  F::constants(tw, md, lane, twg);
+  WP tw[8];
+  F::constants(tw, lane, twg);
   int hy[4], hz[4];   // harmonic held by register reg0167(k) of this lane along y / z, or -1
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -507,7 +540,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, 
         const float2 xa = ra[hy[k]], xb = rb[hy[k]];
         v[reg0167(k)] = {make_float2(xa.x, xb.x), make_float2(xa.y, xb.y)};
       }
-    F::forward<+1>(v, lane, tw, md, mask);
+    F::forward<+1, false>(v, lane, tw, nullptr, mask);
     if (valid) {
       CP *Ar = A + mz * YZP + lane;
 #pragma unroll
@@ -525,7 +558,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, 
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (hz[k] >= 0) v[reg0167(k)] = A[hz[k] * YZP + ry];
-    F::forward<+1>(v, lane, tw, md, mask);
+    F::forward<+1, false>(v, lane, tw, nullptr, mask);
     const float2 *Dc = Dx + ry * 64 + lane;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -533,7 +566,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, 
       v[q].re = f2::mul(v[q].re, d);
       v[q].im = f2::mul(v[q].im, d);
     }
-    F::inverse<-1>(v, lane, tw, md, mask);
+    F::inverse<-1, false>(v, lane, tw, nullptr, mask);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (hz[k] >= 0) A[hz[k] * YZP + ry] = v[reg0167(k)];
@@ -547,7 +580,7 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, 
     const CP *Ar = A + mz * YZP + lane;
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = valid ? Ar[8 * q] : zero;
-    F::inverse<-1>(v, lane, tw, md, mask);
+    F::inverse<-1, false>(v, lane, tw, nullptr, mask);
     if (valid) {
       float2 *ra = Ta + mz * N1, *rb = Tb + mz * N1;
 #pragma unroll
@@ -564,15 +597,16 @@ __global__ void __launch_bounds__(TT) k_yz_t8x2r(Geo g, float2 *__restrict__ T, 
 // MODE 0: Y = X - G u; MODE 1: Y = b - (X - G u); HF = 1 (Eq. 5): G u is
 // replaced by k_m x u / (k_m^2 - k_b^2).  nog = 1 (adjoint of Eq. 4, G
 // already applied in pass 1): G u is replaced by u.
+// (the body of the pass-3 kernels below)
 template <typename R, int L0, int MODE, int TT, int HF>
-__global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T *__restrict__ T,
-                                                 const typename Io<R>::T *__restrict__ X, long long xstride,
-                                                 typename Io<R>::T *__restrict__ Y, long long ystride,
-                                                 const int *__restrict__ act, const Inst *__restrict__ inst,
-                                                 const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,
-                                                 int rows, double *partial, unsigned *counter, double *norm_out,
-                                                 const int *__restrict__ jdev, long long jstride, int pc, int nog,
-                                                 const R *__restrict__ scale) {
+__device__ __forceinline__ void inv_x_t8(Geo g, const typename Cx<R>::T *__restrict__ T,
+                                         const typename Io<R>::T *__restrict__ X, long long xstride,
+                                         typename Io<R>::T *__restrict__ Y, long long ystride,
+                                         const int *__restrict__ act, const Inst *__restrict__ inst,
+                                         const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,
+                                         int rows, double *partial, unsigned *counter, double *norm_out,
+                                         const int *__restrict__ jdev, long long jstride, int pc, int nog,
+                                         const R *__restrict__ scale, int ph) {
   using C = typename Cx<R>::T;
   using IO = typename Io<R>::T;
   using F = Team8<L0>;
@@ -584,14 +618,15 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   __shared__ C bufs[NTM * F::BUF];
   __shared__ double red[32];
   extern __shared__ __align__(16) unsigned char sm_dyn[];
-  C *S3 = reinterpret_cast<C *>(sm_dyn);   // [3][rows][P], then kx[N0], ky[rows], kz[rows]
+  C *S3 = reinterpret_cast<C *>(sm_dyn);   // [3][rows][P], then phase[rows], kx[N0], ky[rows], kz[rows]
   const int b = blockIdx.y;
   if (act && !act[b]) return;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2], P = p3_pitch(N0);
   const int Nh = (int)g.Nh, P2 = N1 * N2;   // 32-bit offsets: 3 Nh < 2^22
   const int r0 = blockIdx.x * rows;
   const int nr = min(rows, P2 - r0);
-  R *kxs = reinterpret_cast<R *>(S3 + 3 * rows * P);
+  C *phs = S3 + 3 * rows * P;   // per row: the conjugate of the shuffle yz pass's factor (ph)
+  R *kxs = reinterpret_cast<R *>(phs + rows);
   R *kys = kxs + N0, *kzs = kys + rows;
   // epilogue mapping: warp per row (rows warp, warp + NW, ...), lane per
   // x harmonic mx = lane + 32 m, m < MXN (2 N0 - 1 <= L0, so N0 <= 32 MXN).
@@ -623,6 +658,12 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
     const int mz = divmod_small(r0 + i, N1, 1.0f / (float)N1, my);
     kys[i] = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
     kzs[i] = (R)(inst[b].kinc[2] + (mz - g.n[2]) * g.K[2]);
+    if constexpr (sizeof(R) == 4) {
+      if (ph) {
+        const C wk = ldg_c(&twg[yz_phase_index(my, g.n[1], mz, g.n[2]) * (TWN / 8)]);
+        phs[i] = mk(wk.x, -wk.y);
+      }
+    }
   }
   {
     // team items (c, row) = divmod(team + i NTM, rows), i < IPT: the loads of
@@ -673,8 +714,15 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
       y2 = cscale(y2, sx);
     }
     const int h = (r0 + row) * N0 + mx;
-    const C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx],
-            u2 = S3[(2 * rows + row) * P + mx];
+    C u0 = S3[(0 * rows + row) * P + mx], u1 = S3[(1 * rows + row) * P + mx], u2 = S3[(2 * rows + row) * P + mx];
+    if constexpr (sizeof(R) == 4) {   // only the complex64 shuffle pass leaves a row factor
+      if (ph) {
+        const C pw = phs[row];
+        u0 = cmul(u0, pw);
+        u1 = cmul(u1, pw);
+        u2 = cmul(u2, pw);
+      }
+    }
     const R kx = kxs[mx], ky = kys[row], kz = kzs[row];
     if (HF) {
       y0 = csub(y0, cscale(csub(cscale(u2, ky), cscale(u1, kz)), id));
@@ -740,6 +788,32 @@ __global__ void __launch_bounds__(TT) k_inv_x_t8(Geo g, const typename Cx<R>::T 
   if (norm_out) last_block_sum((double)acc, red, partial, counter, norm_out, b, gridDim.x, blockIdx.x);
 }
 
+#define GSM_P3_PARAMS                                                                                       \
+  Geo g, const typename Cx<R>::T *__restrict__ T, const typename Io<R>::T *__restrict__ X, long long xstride, \
+      typename Io<R>::T *__restrict__ Y, long long ystride, const int *__restrict__ act,                     \
+      const Inst *__restrict__ inst, const R *__restrict__ iden, const typename Cx<R>::T *__restrict__ twg,  \
+      int rows, double *partial, unsigned *counter, double *norm_out, const int *__restrict__ jdev,          \
+      long long jstride, int pc, int nog, const R *__restrict__ scale, int ph
+#define GSM_P3_ARGS g, T, X, xstride, Y, ystride, act, inst, iden, twg, rows, partial, counter, norm_out, jdev, \
+                    jstride, pc, nog, scale, ph
+template <typename R, int L0, int MODE, int TT, int HF>
+__global__ void __launch_bounds__(TT) k_inv_x_t8(GSM_P3_PARAMS) {
+  inv_x_t8<R, L0, MODE, TT, HF>(GSM_P3_ARGS);
+}
+// complex64: compiled for five 128-thread blocks per SM (96 registers; the
+// epilogue's row factor for the shuffle yz pass would otherwise take 108 and
+// leave four)
+template <typename R, int L0, int MODE, int TT, int HF>
+__global__ void __launch_bounds__(TT, 640 / TT) k_inv_x_t8c(GSM_P3_PARAMS) {
+  inv_x_t8<R, L0, MODE, TT, HF>(GSM_P3_ARGS);
+}
+#undef GSM_P3_PARAMS
+#undef GSM_P3_ARGS
+template <typename R, int L0, int MODE, int TT, int HF> constexpr auto p3_kernel() {
+  if constexpr (sizeof(R) == 4) return &k_inv_x_t8c<R, L0, MODE, TT, HF>;
+  else return &k_inv_x_t8<R, L0, MODE, TT, HF>;
+}
+
 
 template <typename R>
 static int p3_rows(const Geo &g, int tb) {
@@ -749,6 +823,13 @@ static int p3_rows(const Geo &g, int tb) {
 
 
 constexpr int P1_RPT = 2;   // rows per team in pass 1
+
+// whether pass 2 is the complex64 shuffle kernel, which leaves its rows'
+// 8th-root factors to passes 1 and 3 (the same test as pass2's)
+template <typename R> static int yz_phase(const MatvecArgs<R> &a) {
+  if constexpr (sizeof(R) == 4) return (a.Dp && packed_yz_ok(a.g) && a.yzv == 1) ? 1 : 0;
+  else return 0;
+}
 
 // Threads per block of the 128-point kernels: their static team buffers
 // (TT / 16 teams x 144 values) stay under 48 KB for 16-byte values only up
@@ -765,12 +846,12 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
       dim3 gridh((int)(((long long)g.N[2] * g.N[1] + TX / 16 - 1) / (TX / 16)), a.B);
       k_fwd_x_t8h<R, 128, TX><<<gridh, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.inst,
                                                     a.tw, a.jdev, a.jstride, a.form ? 0 : (a.mode >= 2 ? 2 : 1),
-                                                    a.iden);
+                                                    a.iden, yz_phase(a));
     } else {
       const int RB = TX / 16 * P1_RPT;
       dim3 grid((int)((3LL * g.N[2] * g.N[1] + RB - 1) / RB), a.B);
       k_fwd_x_t8<R, 128, TX, P1_RPT><<<grid, TX, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act,
-                                                          a.tw, a.jdev, a.jstride);
+                                                          a.tw, a.jdev, a.jstride, yz_phase(a));
     }
     return;
   }
@@ -782,18 +863,18 @@ static void pass1(const MatvecArgs<R> &a, cudaStream_t st) {
     dim3 gridh((int)(((long long)g.N[2] * g.N[1] + RBH - 1) / RBH), a.B);
     if (g.L[0] == 64)
       k_fwd_x_t8h<R, 64, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.inst,
-                                                   a.tw, a.jdev, a.jstride, op, a.iden);
+                                                   a.tw, a.jdev, a.jstride, op, a.iden, yz_phase(a));
     else
       k_fwd_x_t8h<R, 32, TT><<<gridh, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.inst,
-                                                   a.tw, a.jdev, a.jstride, op, a.iden);
+                                                   a.tw, a.jdev, a.jstride, op, a.iden, yz_phase(a));
     return;
   }
   if (g.L[0] == 64)
     k_fwd_x_t8<R, 64, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.tw,
-                                                       a.jdev, a.jstride);
+                                                       a.jdev, a.jstride, yz_phase(a));
   else
     k_fwd_x_t8<R, 32, TT, P1_RPT><<<grid, TT, 0, st>>>(g, a.X, a.xstride, a.T, a.scale, a.act, a.tw,
-                                                       a.jdev, a.jstride);
+                                                       a.jdev, a.jstride, yz_phase(a));
 }
 
 template <typename R, int TT>
@@ -841,26 +922,26 @@ static void pass3(const MatvecArgs<R> &a, cudaStream_t st) {
   if (g.L[0] == 128) {
     constexpr int TX = tt128<R, TT>();
     const int rows = p3_rows<R>(g, TX);
-    const size_t smem = sizeof(C) * 3 * (size_t)rows * p3_pitch(g.N[0]) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
+    const size_t smem = sizeof(C) * (3 * (size_t)rows * p3_pitch(g.N[0]) + rows) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
     dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);
 #define GSM_P3X(M, HF)                                                                                           \
-  cudaFuncSetAttribute(k_inv_x_t8<R, 128, M, TX, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-  k_inv_x_t8<R, 128, M, TX, HF><<<grid, TX, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,   \
+  cudaFuncSetAttribute(p3_kernel<R, 128, M, TX, HF>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+  p3_kernel<R, 128, M, TX, HF>()<<<grid, TX, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,   \
                                                         a.iden, a.tw, rows, a.partial, a.counter, a.norm_out,     \
-                                                        a.jdev, a.jstride, a.pc, a.mode >= 2, a.scale)
+                                                        a.jdev, a.jstride, a.pc, a.mode >= 2, a.scale, yz_phase(a))
     if (a.form) { if (a.mode & 1) { GSM_P3X(1, 1); } else { GSM_P3X(0, 1); } }
     else { if (a.mode & 1) { GSM_P3X(1, 0); } else { GSM_P3X(0, 0); } }
 #undef GSM_P3X
     return;
   }
   const int rows = p3_rows<R>(g, TT);
-  const size_t smem = sizeof(C) * 3 * (size_t)rows * p3_pitch(g.N[0]) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
+  const size_t smem = sizeof(C) * (3 * (size_t)rows * p3_pitch(g.N[0]) + rows) + sizeof(R) * (g.N[0] + 2 * rows) + 16;
   dim3 grid((int)(((long long)g.N[1] * g.N[2] + rows - 1) / rows), a.B);
 #define GSM_P3(L0, M, HF)                                                                                         \
-  cudaFuncSetAttribute(k_inv_x_t8<R, L0, M, TT, HF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
-  k_inv_x_t8<R, L0, M, TT, HF><<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,     \
+  cudaFuncSetAttribute(p3_kernel<R, L0, M, TT, HF>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+  p3_kernel<R, L0, M, TT, HF>()<<<grid, TT, smem, st>>>(g, a.T, a.X, a.xstride, a.Y, a.ystride, a.act, a.inst,     \
                                                        a.iden, a.tw, rows, a.partial, a.counter, a.norm_out, a.jdev, \
-                                                       a.jstride, a.pc, a.mode >= 2, a.scale)
+                                                       a.jstride, a.pc, a.mode >= 2, a.scale, yz_phase(a))
   if (g.L[0] == 64) {
     if (a.form) { if (a.mode & 1) { GSM_P3(64, 1, 1); } else { GSM_P3(64, 0, 1); } }
     else { if (a.mode & 1) { GSM_P3(64, 1, 0); } else { GSM_P3(64, 0, 0); } }
