@@ -52,7 +52,7 @@ OWN_MV_PC = OWN_MV + 4 * N_HARM[0] ** 3
 # product launch at the bench batch (512 instances), from one ncu capture of
 # the current kernels, per operator; None where no capture of the current
 # kernels exists.
-NCU_TRAFFIC = {"precond": 4.1347e9, "plain": 4.0548e9}
+NCU_TRAFFIC = {"precond": 4.1069e9, "plain": 4.0693e9}
 # FP64 work of one FP64 product of one instance on this grid, from one ncu
 # count of the three FP64 product kernels at 32 instances: floating-point
 # operations (2 DFMA + DADD + DMUL) and FP64-pipe instructions (DFMA + DADD +
@@ -384,7 +384,7 @@ def main():
         achieved = B * B_MV / t_mv / 1e9 if t_mv > 0 else 0.0
         own = (B * own_bytes + 4 * L_FFT ** 3) / t_mv / 1e9 if t_mv > 0 else 0.0
         traffic = NCU_TRAFFIC["precond" if precond else "plain"]
-        return {"kernel": "c64_product (%s + k_yz_t8x2r + k_inv_x_t8)" % ("k_fwd_x_t8h" if precond else "k_fwd_x_t8"),
+        return {"kernel": "c64_product (%s + k_yz_t8x2r + k_inv_x_t8c)" % ("k_fwd_x_t8h" if precond else "k_fwd_x_t8"),
                 "operator": "A M^-1 (as in the solves)" if precond else "A (Eq. 4)",
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind + " (copy, burst)", "traffic": traffic,
