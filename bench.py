@@ -48,6 +48,15 @@ _U = 3 * N_HARM[0] ** 3
 _TSZ = 3 * L_FFT * N_HARM[1] * N_HARM[2]
 OWN_MV = 8 * (_U + _TSZ) + 16 * _TSZ + 8 * (_TSZ + 2 * _U) + 4 * N_HARM[0] ** 3
 OWN_MV_PC = OWN_MV + 4 * N_HARM[0] ** 3
+# FP32-pipe operations (an FMA counts once) of the complex64 yz pass for one
+# instance: per (r_x, c) plane N_z y transforms with inputs pruned to the
+# harmonics, L_z z columns of forward transform, times the real D(r) and
+# inverse transform, and N_z inverse y transforms with pruned outputs.  Per
+# lane of a 64-point transform (radix 8 x 8, seven twiddle products of four
+# operations): forward 36 (8-point DFT of four nonzero inputs) + 28 + 52,
+# inverse 52 + 28 + 44 (four kept outputs); D is two operations per value.
+_YZ_T = 8 * ((36 + 28 + 52) + (52 + 28 + 44))
+OPS_YZ = 3 * L_FFT * ((N_HARM[0] + L_FFT) * _YZ_T + 2 * L_FFT * L_FFT)
 # dram__bytes_read.sum + dram__bytes_write.sum of the three kernels of one
 # product launch at the bench batch (512 instances), from one ncu capture of
 # the current kernels, per operator; None where no capture of the current
@@ -397,6 +406,14 @@ def main():
     # the preconditioner exists for Eq. 4 only: an Eq. 5 solve iterates with the plain operator
     pc_solve = args.precond != "none" and args.form == "e"
     roof = product_roofline(pc_solve, OWN_MV_PC if pc_solve else OWN_MV, "roofline_product")
+    fma32 = gsm.probe_fma(1, local, stream.cuda_stream)
+    # the yz pass, compute-bound: FP32-pipe operations against the measured
+    # FMA instruction rate (the probe's flop rate / 2)
+    t_yz = roof["passes_us"]["yz_conv"] * 1e-6
+    roof_yz = {"kernel": "k_yz_t8x2r", "bound": "alu", "unit": "Top/s (FP32-pipe lane operations)",
+               "ops_per_instance": OPS_YZ, "achieved": B * OPS_YZ / t_yz / 1e12 if t_yz > 0 else None,
+               "peak": fma32 / 2, "peak_kind": "measured (gsm_probe_fma FP32 / 2)",
+               "frac": (B * OPS_YZ / t_yz / 1e12) / (fma32 / 2) if t_yz > 0 else None, "avg_us": 1e6 * t_yz}
     roof_plain = product_roofline(False, OWN_MV, "roofline_product_plain") if pc_solve else None
     # Gram-Schmidt passes (dots + update) inside the profiled solve, at the
     # algorithmic bytes of the instances still iterating at each step
@@ -422,7 +439,7 @@ def main():
         "fp64_plain": None if fp64_value is None else
         {"value": fp64_value, "unit": "solves/s", "iters_mean": float(np.mean([i["iters"] for i in infos64])),
          "roofline": fp64_roof},
-        "measured_fma_tflops": {"fp32": gsm.probe_fma(1, local, stream.cuda_stream),
+        "measured_fma_tflops": {"fp32": fma32,
                                 "fp32x2": gsm.probe_fma(2, local, stream.cuda_stream)},
         "speedup_vs_fp64": None if fp64_value is None else value / ws / fp64_value,
         "alt_krylov": alt_line,
@@ -430,6 +447,7 @@ def main():
         "rel_residual_max": float(max(i["rel_residual"] for i in infos)),
         "roofline": roof,
         "roofline_plain_operator": roof_plain,
+        "roofline_yz": roof_yz,
         "roofline_krylov": {"kernel": "k_dots + k_update", "bound": "hbm",
                             "achieved": kr_by / (kr_ms / 1000.0) / 1e9 if kr_ms > 0 else None,
                             "peak": peak, "unit": "GB/s",
