@@ -364,16 +364,19 @@ __global__ void __launch_bounds__(KT) k_sol_update(double2 *__restrict__ x64, lo
   C *Vb = V + b * vinst;
   double2 *xb = x64 + b * xinst;
   C *dv = dslot >= 0 ? Vb + (long long)dslot * Us : nullptr;   // keeps the correction d for r -= A d
-  double acc = 0;   // ||d||^2: bounds the rounding error of a later r -= A d
+  // ||d||^2: bounds the rounding error of a later r -= A d (a few digits
+  // suffice: summed in the basis precision per thread, FP64 across threads)
+  R acc = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < U; e += (long long)gridDim.x * blockDim.x) {
+    const double2 xv = xb[e];   // fetched first: its load overlaps the basis loads
     C d = mk((R)0, (R)0);
+#pragma unroll 4
     for (int i = 0; i < n; ++i) d = cadd(d, cmul(ys[i], Vb[(long long)i * Us + e]));
-    double2 xv = xb[e];
     xb[e] = mk(xv.x + (double)d.x, xv.y + (double)d.y);
     if (dv) dv[e] = d;
-    acc += (double)d.x * d.x + (double)d.y * d.y;
+    acc += d.x * d.x + d.y * d.y;
   }
-  last_block_sum(acc, red, partial, counter, dnorm2, b, gridDim.x, blockIdx.x);
+  last_block_sum((double)acc, red, partial, counter, dnorm2, b, gridDim.x, blockIdx.x);
 }
 
 // Right-preconditioned Krylov cycles solve A M^{-1} u = r, so the
@@ -408,8 +411,14 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
   const C *V0 = Vb + (src >= 0 ? (long long)src * Us : 0);
   const long long Nh = g.Nh;
   const R pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
-  double acc = 0;   // ||M^{-1} u||^2, the correction added to x
+  // ||M^{-1} u||^2, the correction added to x: summed in FP32 per thread (it
+  // bounds the rounding of recursive residual updates, with a factor 10 to
+  // spare) and in FP64 across threads
+  float acc = 0.f;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < Nh; e += (long long)gridDim.x * blockDim.x) {
+    double2 xv[3];   // the iterate, fetched before the basis so that its loads overlap theirs
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xv[c] = xb[c * Nh + e];
     C d[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) d[c] = mk((R)0, (R)0);
@@ -433,7 +442,8 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
     if (dv)
 #pragma unroll
       for (int c = 0; c < 3; ++c) dv[c * Nh + e] = d[c];
-    const int row = (int)(e / g.N[0]), mx = (int)(e - (long long)row * g.N[0]);
+    const int ei = (int)e;   // Nh < 2^31
+    const int row = ei / g.N[0], mx = ei - row * g.N[0];
     const int mz = row / g.N[1], my = row - mz * g.N[1];
     const R kx = (R)(inst[b].kinc[0] + (mx - g.n[0]) * g.K[0]);
     const R ky = (R)(inst[b].kinc[1] + (my - g.n[1]) * g.K[1]);
@@ -445,13 +455,12 @@ __global__ void __launch_bounds__(KT) k_sol_update_pc(Geo g, const Inst *__restr
     const R kc[3] = {kx, ky, kz};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double2 xv = xb[c * Nh + e];
-      const double cx = (double)(al * d[c].x + f * kc[c] * kr), cy = (double)(al * d[c].y + f * kc[c] * ki);
-      xb[c * Nh + e] = mk(xv.x + cx, xv.y + cy);
-      acc += cx * cx + cy * cy;
+      const R cx = al * d[c].x + f * kc[c] * kr, cy = al * d[c].y + f * kc[c] * ki;
+      xb[c * Nh + e] = mk(xv[c].x + (double)cx, xv[c].y + (double)cy);
+      acc += (float)(cx * cx + cy * cy);
     }
   }
-  last_block_sum(acc, red, partial, counter, dnorm2, b, gridDim.x, blockIdx.x);
+  last_block_sum((double)acc, red, partial, counter, dnorm2, b, gridDim.x, blockIdx.x);
 }
 
 // r -= A d with A d from the complex64 product, and ||r||^2 (last block).
