@@ -700,10 +700,6 @@ __device__ __forceinline__ void inv_x_t8(Geo g, const typename Cx<R>::T *__restr
   }
   __syncthreads();
   const R kb2 = (R)inst[b].kb2, pcc = (R)inst[b].pc_c, pcb = (R)inst[b].pc_beta;
-  // the source E^inc_0 = a of MODE 1, converted once per thread (inside the
-  // per-harmonic branch the conversions were evaluated for every harmonic)
-  const C sa0 = mk((R)inst[b].a[0], (R)inst[b].a[1]), sa1 = mk((R)inst[b].a[2], (R)inst[b].a[3]),
-          sa2 = mk((R)inst[b].a[4], (R)inst[b].a[5]);
   const int h0 = (g.n[2] * N1 + g.n[1]) * N0 + g.n[0];
   IO *Yb = Y + b * ystride;
   R acc = 0;   // this thread's share of ||y||^2 (a few harmonics), widened once
@@ -760,9 +756,9 @@ __device__ __forceinline__ void inv_x_t8(Geo g, const typename Cx<R>::T *__restr
     if (MODE == 1) {
       C a0 = mk((R)0, (R)0), a1 = a0, a2 = a0;
       if (h == h0) {
-        a0 = sa0;
-        a1 = sa1;
-        a2 = sa2;
+        a0 = mk((R)inst[b].a[0], (R)inst[b].a[1]);
+        a1 = mk((R)inst[b].a[2], (R)inst[b].a[3]);
+        a2 = mk((R)inst[b].a[4], (R)inst[b].a[5]);
       }
       y0 = mk(a0.x - y0.x, a0.y - y0.y);
       y1 = mk(a1.x - y1.x, a1.y - y1.y);
