@@ -13,6 +13,11 @@
 //                        row (y inverse)
 //   pass 3  k_inv_x_t8 : team per (c, row): L_x -> N_x, then per harmonic
 //                        the Green tensor and y = x - G u (or the residual)
+//
+// complex64 on 64-point y and z grids runs pass 2 as k_yz_t8x2r (two x
+// frequencies per block in packed FP32 pairs, lane-shuffle transposes), which
+// leaves an 8th-root factor per (m_z, m_y) row of the intermediate that pass 1
+// applies (yz_phase_index) and pass 3 removes (k_inv_x_t8c).
 #pragma once
 #include "fft_team8.cuh"
 #include "fft_team8x2.cuh"
