@@ -1085,6 +1085,7 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
   // since the last certified residual: the rounding error of those updates
   // is at most EPS_MV_C64 times it
   std::vector<double> dsum(B, 0.0);
+  const double epsmv = eps_mv();
   // instances whose recursive residual met the target but could not certify
   // it: they need the certified residual b - A x, not another Krylov cycle
   std::vector<char> verify(B, 0);
@@ -1380,7 +1381,7 @@ static gsm_status solve_batch(gsm_plan_t *p, const std::vector<Part> &parts, int
       bool trusted = true;
       if (recursive) {
         dsum[b] += std::sqrt(std::max(h_dn[b], 0.0));
-        trusted = eps_mv() * dsum[b] <= 0.1 * tol * bnorm[b];
+        trusted = epsmv * dsum[b] <= 0.1 * tol * bnorm[b];
         if (!trusted) cert_ok[b] = 0;
       } else {
         dsum[b] = 0.0;
